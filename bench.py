@@ -1,0 +1,396 @@
+"""Benchmark: decoded pixels/s of the batched wavefront + adjacent-patch decoder.
+
+Workload (one step = one decode of the whole batch through the hot path):
+one 2048x2048 and eight 1024x1024 RGB images from the seeded generator
+(seed 4, 64 polygons each), coded in independent 256x256 patches with one
+rANS stream per patch row, h=3, C=64, 2 residual blocks, K=10, BF16 network
+on tcgen05 tensor cores with FP32 mixture/CDF and integer rANS.  The model is
+first trained in-run on seeded 32x32 crops (no pretrained weights exist).
+
+Reported next to the decoder: the same containers decoded sequentially on the
+same GPU (one pixel per image per step, the paper's sequential decoder), the
+encoder's throughput, code lengths (actual bytes and model-ideal), the FP64
+oracle's code length on sampled pixels, a roofline line for the decode
+kernel, an end-to-end number through the C ABI with host buffers, and the
+oracle decoder timed on a bounded sample on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded pixels/s and bpd vs same-GPU sequential decode, 32^2-2048^2 RGB"
+UNIT = "decoded px/s"
+CFG = (3, 64, 2, 10)
+PATCH = 256
+SIZES = [(2048, 2048)] + [(1024, 1024)] * 8
+SEED = 4
+N_POLY = 64
+L2_BYTES = 129 * 2 ** 20
+
+
+def workload_name():
+    return "1x2048^2 + 8x1024^2 RGB, 256^2 patches, h=3 C=64 R=2 K=10, BF16 net"
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(rank=0):
+    from paper_2201_05213_gb300 import synth
+    return synth.make_batch(SEED + 1000 * rank, SIZES, N_POLY)
+
+
+def train_model(codec, steps, batch=64, lr=2e-3, seed=1):
+    """In-run maximum-likelihood training on seeded 32x32 crops (Eq. 2)."""
+    import torch
+    from paper_2201_05213_gb300 import synth
+    pool = torch.from_numpy(synth.random_crops(seed, 4096, size=32, source=256)).cuda()
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    last = None
+    for s in range(steps):
+        idx = torch.randint(0, pool.shape[0], (batch,), generator=g).cuda()
+        last = codec.train_step(pool[idx].contiguous(), lr if s < steps * 3 // 4 else lr / 4,
+                                want_loss=(s == steps - 1))
+    return last
+
+
+def oracle_sample_bpd(w, imgs, n=256, seed=0):
+    """FP64 oracle model code length (bits/dim) of n sampled pixels, patch units."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    tot = 0.0
+    per = []
+    for k in range(n):
+        i = int(rng.integers(0, len(imgs)))
+        H, W = imgs[i].shape[:2]
+        y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
+        P = O.forward_pixels(CFG, w, imgs[i], [y], [x], patch=PATCH)[0]
+        b = O.pixel_bits(CFG[3], P, *imgs[i][y, x])
+        per.append((i, y, x, b))
+        tot += b
+    return tot / (3 * n), per
+
+
+def cpu_baseline(w, img, budget_s=12.0):
+    """The oracle's sequential decoder on a bounded sample (first rows of the
+    first 256x256 patch, decoded as one unit) on one host core."""
+    import oracle as O
+    rows = 8
+    sub = np.ascontiguousarray(img[:rows, :PATCH])
+    words, lens, _, _ = O.encode_image(CFG, w, sub, 0, 1)
+    t0 = time.perf_counter()
+    dec, ok = O.decode_image(CFG, w, words, lens, rows, PATCH, 0, 1)
+    dt = time.perf_counter() - t0
+    assert ok and (dec == sub).all()
+    # grow the sample to fill roughly the budget
+    if dt < budget_s / 4:
+        rows = int(min(PATCH, max(rows, rows * budget_s / max(dt, 1e-3) / 2)))
+        sub = np.ascontiguousarray(img[:rows, :PATCH])
+        words, lens, _, _ = O.encode_image(CFG, w, sub, 0, 1)
+        t0 = time.perf_counter()
+        dec, ok = O.decode_image(CFG, w, words, lens, rows, PATCH, 0, 1)
+        dt = time.perf_counter() - t0
+        assert ok and (dec == sub).all()
+    px = rows * PATCH
+    return {"value": px / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rows}x{PATCH} px of the first 256^2 patch of the 2048^2 image, "
+                      f"sequential FP64 decode, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2201_05213_gb300 import synth
+    w = synth.xavier_weights(*CFG, seed=0)
+    img = synth.make_image(SEED, 2048, 2048, N_POLY, index=0)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(w, img, budget_s=4.0))
+    timed = vals[args.warmup:]
+    v = float(np.mean([t["value"] for t in timed]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * (2048 * 2048 + 8 * 1024 * 1024) / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(), "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": timed[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nlc", choices=["nlc", "reference"])
+    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--no-seq", action="store_true", help="skip the sequential baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2201_05213_gb300 import codec as CD
+    from paper_2201_05213_gb300 import nlc as N
+    from paper_2201_05213_gb300 import synth
+
+    dev = torch.device("cuda", local)
+    imgs = make_workload(rank)
+    n_px = sum(h * w for h, w in SIZES)
+    w0 = synth.xavier_weights(*CFG, seed=0)
+    codec = CD.Codec(*CFG, N.NLC_BF16, w0)
+    t0 = time.perf_counter()
+    train_loss = train_model(codec, args.train_steps) if args.train_steps > 0 else None
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    w = codec.get_weights()
+
+    dimgs = [torch.from_numpy(i).to(dev) for i in imgs]
+    stream = torch.cuda.current_stream()
+    # encoder
+    data, offs = codec.compress(dimgs, PATCH, N.NLC_LAYOUT_ROW)
+    torch.cuda.synchronize()
+    te0 = torch.cuda.Event(enable_timing=True)
+    te1 = torch.cuda.Event(enable_timing=True)
+    te0.record(stream)
+    data, offs = codec.compress(dimgs, PATCH, N.NLC_LAYOUT_ROW, check=False)
+    te1.record(stream)
+    codec.check()
+    enc_ms = te0.elapsed_time(te1)
+    total_bytes = int(offs[-1])
+    outs = [torch.empty_like(t) for t in dimgs]
+    sizes = SIZES
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    def decode():
+        N.nlc_decompress(codec.ctx, data, offs, outs, PATCH, N.NLC_LAYOUT_ROW,
+                         N.NLC_SCHED_WAVEFRONT, stream)
+
+    for _ in range(args.warmup):
+        decode()
+    codec.check()
+    for a, b in zip(outs, imgs):
+        assert np.array_equal(a.cpu().numpy(), b), "round trip differs"
+    times = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            decode()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    codec.check()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    value = world * n_px / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers
+    h_data = data[:total_bytes].cpu().pin_memory()
+    h_offs = offs.cpu().pin_memory()
+    h_outs = [torch.empty(t.shape, dtype=torch.uint8).pin_memory() for t in dimgs]
+    d_in = torch.empty(total_bytes, dtype=torch.uint8, device=dev)
+    d_offs = torch.empty_like(offs)
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_in.copy_(h_data, non_blocking=True)
+        d_offs.copy_(h_offs, non_blocking=True)
+        N.nlc_decompress(codec.ctx, d_in, d_offs, outs, PATCH, N.NLC_LAYOUT_ROW,
+                         N.NLC_SCHED_WAVEFRONT, stream)
+        for ho, do in zip(h_outs, outs):
+            ho.copy_(do, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(e0.elapsed_time(e1))
+    codec.check()
+    for a, b in zip(h_outs, imgs):
+        assert np.array_equal(a.numpy(), b), "end-to-end round trip differs"
+    e2e_ms = float(np.mean(e2e_times))
+
+    # code lengths
+    _, bits = codec.forward(dimgs, PATCH, params=False, bits=True)
+    dims = 3 * n_px
+    gpu_model_bpd = float(bits.double().sum()) / dims
+    actual_bpd = 8.0 * total_bytes / dims
+
+    extra = {}
+    if rank == 0:
+        # sequential baseline: same containers, one pixel per image per step
+        if not args.no_seq:
+            torch.cuda.synchronize()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            N.nlc_decompress(codec.ctx, data, offs, outs, PATCH, N.NLC_LAYOUT_ROW,
+                             N.NLC_SCHED_SEQUENTIAL, stream)
+            s1.record(stream)
+            s1.synchronize()
+            codec.check()
+            seq_ms = s0.elapsed_time(s1)
+            for a, b in zip(outs, imgs):
+                assert np.array_equal(a.cpu().numpy(), b), "sequential round trip differs"
+            extra["sequential_baseline"] = {
+                "value": n_px / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms,
+                "steps": 2048 * 2048, "speedup": seq_ms / ms,
+                "how": "same library and containers, NLC_SCHED_SEQUENTIAL (one pixel per image "
+                       "per step, patches of an image one after another), one full run"}
+        oracle_bpd, _ = oracle_sample_bpd(w.astype(np.float64), imgs, n=192)
+        sample_idx = np.random.default_rng(0)
+        # GPU model bits on the same sampled pixels
+        rng = np.random.default_rng(0)
+        bits_np = bits.cpu().numpy()
+        base = np.cumsum([0] + [h * w_ for h, w_ in SIZES])
+        gsum = 0.0
+        for k in range(192):
+            i = int(rng.integers(0, len(imgs)))
+            H, W = imgs[i].shape[:2]
+            y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
+            gsum += float(bits_np[base[i] + y * W + x])
+        extra["bpd"] = {"actual": actual_bpd, "gpu_model": gpu_model_bpd,
+                        "oracle_model_sample": oracle_bpd, "gpu_model_sample": gsum / (3 * 192),
+                        "sample": "192 random pixels"}
+        extra["encode"] = {"value": n_px / (enc_ms / 1e3), "unit": "encoded px/s", "ms": enc_ms}
+        extra["train"] = {"steps": args.train_steps, "seconds": train_s, "final_loss_bpd": train_loss}
+
+    peaks, src = _measured_peaks()
+    # roofline of the decode kernel: MUFU-bound CDF evaluation
+    evals_per_px = 3 * 255 * CFG[3]
+    mufu_ops = 2.0 * evals_per_px * n_px
+    clk = clk.summary()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    mufu_peak = 16 * 152 * sm_mhz * 1e6  # 16 MUFU lanes / clk / SM
+    achieved = mufu_ops / (ms / 1e3)
+    flops = 54784.0 * n_px
+    roof = {"bound": "alu", "unit": "MUFU op/s", "achieved": achieved, "peak": mufu_peak,
+            "frac": achieved / mufu_peak, "traffic": None,
+            "peak_source": f"16 MUFU lanes/clk/SM x 152 SMs x {sm_mhz:.0f} MHz (max SM clock)",
+            "tensor": {"achieved_tflops": flops / (ms / 1e3) / 1e12,
+                       "peak_tflops": peaks.get("bf16_tflops_sustained"),
+                       "frac": flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops_sustained", 1700),
+                       "peak_source": src}}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded generator; model "
+            "trained in-run on seeded crops)",
+            "config": {"workload": workload_name(), "images": len(SIZES), "pixels": n_px,
+                       "patch": PATCH, "units": 192, "h": CFG[0], "C": CFG[1], "R": CFG[2],
+                       "K": CFG[3], "schedule": "wavefront", "layout": "row streams",
+                       "l2": "flushed before every timed step (256 MiB write)"},
+            "roofline": roof,
+            "e2e": {"value": world * n_px / (e2e_ms / 1e3), "unit": UNIT, "ms": e2e_ms,
+                    "h2d_bytes_per_step": total_bytes + 8 * (len(SIZES) + 1),
+                    "d2h_bytes_per_step": 3 * n_px},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clk,
+            **extra,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(w.astype(np.float64), imgs[0])
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * nlc.h -- C ABI of the GB300 (sm_103a) parallel local-autoregressive image
+ * compressor ("Parallel Neural Local Lossless Compression", Zhang, Townsend,
+ * Kang, Barber).
+ *
+ * Model (Section 2.1, Eq. 3): pixel (i, j) of a coding unit depends only on
+ * rows i-h..i-1, columns j-h..j+h and on row i, columns j-h..j-1 (zero
+ * outside the unit).  The local PixelCNN is a masked first layer over that
+ * context (3 -> C channels), n_res residual blocks of two 1x1 layers with ELU,
+ * and a 1x1 head to a K-component discretized logistic mixture with
+ * channel-coupled RGB means.  Stream coder: 32-bit rANS (ANS, Section 2),
+ * one stream per unit row.  Decoding follows Algorithm 1 (Section 3): at step
+ * t every pixel with j = t - (h+1) i is decoded in one batch, so an H x W
+ * unit takes W + (H-1)(h+1) steps instead of H W; independent P x P patches
+ * of an image are decoded concurrently.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers on the current CUDA device;
+ *     h_* are host pointers.  The caller owns every buffer it passes; the
+ *     library owns only the context and a device workspace that it grows on
+ *     demand (so the first call with a larger batch allocates).
+ *   - Images are uint8 H x W x 3 (RGB), C-contiguous, row stride 3 W bytes.
+ *   - Calls taking a `stream` are asynchronous on that stream (NULL = the
+ *     legacy default stream).  Argument errors are detected synchronously and
+ *     returned.  Errors found on the device (corrupt stream, weight mismatch,
+ *     capacity overflow, a bounded wait that timed out) are recorded in the
+ *     context's device status word and returned by nlc_sync_status().
+ *   - Calls on one context must not overlap on different streams: they share
+ *     the context's workspace.
+ *   - Every function returns an nlc_status; nlc_last_error() describes the
+ *     last failure of the calling thread.
+ */
+#ifndef NLC_H
+#define NLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NLC_ABI_VERSION 1
+
+typedef struct nlc_ctx nlc_ctx;
+typedef struct CUstream_st* nlc_stream;
+
+typedef enum {
+  NLC_OK = 0,
+  NLC_ERR_ARG = 1,         /* invalid argument (synchronous)                 */
+  NLC_ERR_CAPACITY = 2,    /* output buffer too small                        */
+  NLC_ERR_CORRUPT = 3,     /* malformed container or rANS stream            */
+  NLC_ERR_WEIGHTS = 4,     /* container made with other weights / precision */
+  NLC_ERR_CUDA = 5,        /* a CUDA call failed                             */
+  NLC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                  */
+  NLC_ERR_UNSUPPORTED = 7  /* configuration outside the compiled limits     */
+} nlc_status;
+
+typedef enum { NLC_FP32 = 0, NLC_BF16 = 1 } nlc_precision;
+
+/* Decode schedules.  All three decode the same container to the same pixels
+ * (Section 4: every schedule has the same compression rate). */
+typedef enum {
+  NLC_SCHED_RASTER = 0,      /* one pixel per unit per step, raster order      */
+  NLC_SCHED_WAVEFRONT = 1,   /* Algorithm 1: the whole front j = t-(h+1)i     */
+  NLC_SCHED_SEQUENTIAL = 2   /* one pixel per image per step: the units of an
+                                image one after another, raster inside each
+                                (the paper's sequential decoder)             */
+} nlc_schedule;
+
+/* Stream layouts. */
+typedef enum {
+  NLC_LAYOUT_UNIT = 0,  /* one stream per unit, raster order (sequential only) */
+  NLC_LAYOUT_ROW = 1    /* one stream per unit row: decodable by every schedule */
+} nlc_layout;
+
+/* Model configuration: horizon h (1..3), channels C (16, 32, 48 or 64),
+ * residual blocks n_res (0..4), mixture components K (1..16), network
+ * precision (FP32 SIMT, or BF16 on tcgen05 tensor cores with FP32
+ * accumulation).  The mixture, CDF and coder are FP32/integer in both. */
+typedef struct {
+  int32_t h, C, n_res, K, precision;
+} nlc_model_cfg;
+
+typedef struct {
+  const uint8_t* data; /* device pointer, H x W x 3 */
+  int32_t H, W;
+} nlc_image_in;
+
+typedef struct {
+  uint8_t* data; /* device pointer, H x W x 3, written by the decoder */
+  int32_t H, W;
+} nlc_image_out;
+
+/* Thread-local description of the last error (never NULL). */
+const char* nlc_last_error(void);
+int nlc_abi_version(void);
+
+/* Number of FP32 weights of cfg; the flat layout is
+ *   W0[C][F] b0[C] { W1[C][C] b1[C] W2[C][C] b2[C] } x n_res WH[10K][C] bH[10K]
+ * with F = 6h(h+1): feature 3p + c of W0 is channel c of context tap p, the
+ * taps enumerating rows -h..-1 (columns -h..h) then row 0 (columns -h..-1),
+ * i.e. the unmasked taps of a (2h+1)^2 type-A masked kernel in raster order.
+ * Head outputs: [0,K) mixture logits, [K,4K) means, [4K,7K) log-scales
+ * (clamped at -7), [7K,10K) raw coupling coefficients (tanh).  Returns 0 for
+ * an invalid cfg. */
+size_t nlc_num_weights(const nlc_model_cfg* cfg);
+
+/* Creates a context on the current device with the given host weights
+ * (n_weights must equal nlc_num_weights(cfg)).  Synchronous. */
+int nlc_create(const nlc_model_cfg* cfg, const float* h_weights, size_t n_weights, nlc_ctx** out);
+int nlc_destroy(nlc_ctx* ctx);
+
+/* Copies the current FP32 weights to / from the host (synchronous).  Setting
+ * weights also resets the optimizer state. */
+int nlc_get_weights(nlc_ctx* ctx, float* h_weights, size_t n_weights);
+int nlc_set_weights(nlc_ctx* ctx, const float* h_weights, size_t n_weights);
+
+/* 64-bit content hash of (cfg, weights), stored in every container. */
+int nlc_weight_hash(nlc_ctx* ctx, uint64_t* h_hash);
+
+/* Waits for `stream`, returns the device status recorded since the last call
+ * (NLC_OK if none) and clears it. */
+int nlc_sync_status(nlc_ctx* ctx, nlc_stream stream);
+
+/* Decoder tuning: the decoder assigns about px_per_cta pixels of every step
+ * to each CTA (default 8) and uses at most max_ctas CTAs (0 = as many as can
+ * be co-resident). */
+int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
+
+/* Upper bound of the compressed size of n images with the given sizes, unit
+ * partition and layout: per image 32 + 4 n_streams + 6 H W + 4 n_streams
+ * bytes, rounded up to 16.  `patch` = side of the square coding units (0 =
+ * the whole image is one unit). */
+int nlc_compress_bound(const int32_t* h_H, const int32_t* h_W, int n, int patch, int layout,
+                       size_t* h_bytes);
+
+/* Compresses n images.  Container i is written to d_out + d_offsets[i] and
+ * ends at d_offsets[i+1]; d_offsets (n+1 uint64, device) is written by the
+ * library.  Container: 32-byte header ("NLC1", version, h, layout,
+ * precision, H, W, patch, n_streams, weight hash), n_streams uint32 stream
+ * lengths, the streams (rANS, 4-byte big-endian final state then bytes),
+ * zero padding to 16 bytes.  If the total exceeds `cap` nothing is written
+ * and the device status becomes NLC_ERR_CAPACITY (d_offsets still holds the
+ * sizes).  The encoder computes every pixel's frequency tables in parallel
+ * with the decoder's own device code (the paper's encoder reruns the
+ * decoder's procedure for the same reason, Section 4). */
+int nlc_compress(nlc_ctx* ctx, const nlc_image_in* h_imgs, int n, int patch, int layout,
+                 uint8_t* d_out, size_t cap, uint64_t* d_offsets, nlc_stream stream);
+
+/* Decompresses n containers (d_in + d_offsets[i] .. d_offsets[i+1]) into
+ * caller-allocated images whose H, W must match the containers.  `patch`
+ * and `layout` must be those used to compress; `schedule` is an
+ * nlc_schedule (NLC_LAYOUT_UNIT needs RASTER or SEQUENTIAL).  The wavefront
+ * decode is one persistent cooperative kernel: the pixels of every step are
+ * split across all CTAs, which meet at a bounded grid barrier between steps. */
+int nlc_decompress(nlc_ctx* ctx, const uint8_t* d_in, const uint64_t* d_offsets,
+                   const nlc_image_out* h_outs, int n, int patch, int layout, int schedule,
+                   nlc_stream stream);
+
+/* Network outputs (d_params: sum H W x 10K floats, images in order, pixels
+ * in raster order) and/or the model code length -log2 p(x_ij) of every pixel
+ * (d_bits: sum H W floats); either may be NULL.  Context zero outside the
+ * units of the given patch partition. */
+int nlc_forward(nlc_ctx* ctx, const nlc_image_in* h_imgs, int n, int patch, float* d_params,
+                float* d_bits, nlc_stream stream);
+
+/* Frequency tables of n pixels from given network outputs (d_params: n x 10K)
+ * and pixel values (d_pixels: n x 3): d_cum (n x 3 x 257 uint32) receives
+ * cum_0..cum_256 of the R, G|r and B|r,g coding distributions. */
+int nlc_tables(nlc_ctx* ctx, const float* d_params, const uint8_t* d_pixels, int64_t n,
+               uint32_t* d_cum, nlc_stream stream);
+
+/* rANS stage alone.  Stream s codes symbols [d_sym_off[s], d_sym_off[s+1])
+ * given as (start, freq) with 16-bit probability scale; it is written to the
+ * LAST d_len[s] bytes of the slot d_bytes + s * stride (stride >= 2 nsym + 4). */
+int nlc_rans_encode(const uint32_t* d_start, const uint32_t* d_freq, const int64_t* d_sym_off,
+                    int n_streams, uint8_t* d_bytes, int64_t stride, int32_t* d_len,
+                    nlc_stream stream);
+
+/* Decodes the streams laid out as nlc_rans_encode writes them, with one
+ * cumulative table (257 uint32) per symbol.  A stream that does not end in
+ * the initial state with every byte consumed sets NLC_ERR_CORRUPT in the
+ * context's status (ctx may not be NULL). */
+int nlc_rans_decode(nlc_ctx* ctx, const uint8_t* d_bytes, int64_t stride, const int32_t* d_len,
+                    const uint32_t* d_cum, const int64_t* d_sym_off, int n_streams,
+                    int32_t* d_sym, nlc_stream stream);
+
+/* Maximum-likelihood training (Eq. 2).  One Adam step (beta 0.9/0.999,
+ * eps 1e-8) on the mean code length in bits per dimension of N H x W images
+ * (d_batch, each image one unit); h_loss (may be NULL) receives the loss
+ * before the step, which makes the call synchronous. */
+int nlc_train_step(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, float lr,
+                   float* h_loss, nlc_stream stream);
+
+/* Loss (bits per dimension, d_loss: 1 float) and its gradient with respect
+ * to the FP32 weights (d_grad: nlc_num_weights floats) -- the adjoint of the
+ * network and of the mixture likelihood. */
+int nlc_loss_grad(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, float* d_loss,
+                  float* d_grad, nlc_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLC_H */

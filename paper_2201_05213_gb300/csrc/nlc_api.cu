@@ -1,0 +1,586 @@
+// Host side of the nlc C ABI (include/nlc.h): argument validation, the
+// context (weights, optimizer state, device workspace), batch planning
+// (coding units, streams, schedules) and kernel launches.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/nlc.h"
+#include "nlc_common.cuh"
+#include "nlc_kernels.cuh"
+#include "nlc_model.cuh"
+#include "nlc_tc.cuh"
+#include "nlc_train.cuh"
+
+using namespace nlc;
+
+static thread_local char g_err[512] = "no error";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                  \
+  do {                                                                               \
+    cudaError_t e_ = (x);                                                            \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(NLC_ERR_CUDA, "%s failed: %s", #x, cudaGetErrorString(e_));        \
+  } while (0)
+
+struct nlc_ctx {
+  Dims d;
+  int device = 0, sm_count = 0;
+  size_t n_w = 0;
+  float* d_w = nullptr;
+  float* d_simt = nullptr;
+  uint16_t* d_umma = nullptr;
+  float* d_bias = nullptr;
+  unsigned long long* d_hash = nullptr;
+  int* d_status = nullptr;
+  float* d_m = nullptr;  // Adam moments
+  float* d_v = nullptr;
+  float* d_grad = nullptr;
+  float* d_loss = nullptr;
+  long long adam_t = 0;
+  bool dirty = true;
+  unsigned char* ws = nullptr;
+  size_t ws_cap = 0;
+  int px_per_cta = 8;
+  int max_ctas = 0;
+};
+
+extern "C" const char* nlc_last_error(void) { return g_err; }
+extern "C" int nlc_abi_version(void) { return NLC_ABI_VERSION; }
+
+static bool cfg_ok(const nlc_model_cfg* c) {
+  return c && c->h >= 1 && c->h <= kMaxH && (c->C == 16 || c->C == 32 || c->C == 48 ||
+                                               c->C == 64) &&
+         c->n_res >= 0 && c->n_res <= kMaxR && c->K >= 1 && c->K <= kMaxK &&
+         (c->precision == NLC_FP32 || c->precision == NLC_BF16);
+}
+
+static Dims make_dims(const nlc_model_cfg* c) {
+  Dims d;
+  d.h = c->h;
+  d.C = c->C;
+  d.R = c->n_res;
+  d.K = c->K;
+  d.F = 6 * c->h * (c->h + 1);
+  d.Fp = (d.F + 15) / 16 * 16;
+  d.NO = 10 * c->K;
+  d.NOp = (d.NO + 15) / 16 * 16;
+  d.ldP = d.NOp + 4;
+  d.prec = c->precision;
+  return d;
+}
+
+extern "C" size_t nlc_num_weights(const nlc_model_cfg* c) {
+  if (!cfg_ok(c)) return 0;
+  const size_t F = 6 * c->h * (c->h + 1), C = c->C;
+  return C * F + C + (size_t)c->n_res * 2 * (C * C + C) + 10 * (size_t)c->K * C + 10 * (size_t)c->K;
+}
+
+static DeviceModel model_view(const nlc_ctx* x) {
+  DeviceModel m;
+  m.d = x->d;
+  m.w.simt = x->d_simt;
+  m.w.umma = x->d_umma;
+  m.w.bias = x->d_bias;
+  m.w.simt_floats = (int)simt_floats(x->d);
+  m.w.umma_halves = (int)umma_halves(x->d);
+  m.hash = x->d_hash;
+  return m;
+}
+
+static int ensure_packed(nlc_ctx* x, cudaStream_t s) {
+  if (!x->dirty) return NLC_OK;
+  CUDA_TRY(launch_repack(x->d, x->d_w, x->d_simt, x->d_umma, x->d_bias, x->d_hash, (int)x->n_w, s));
+  x->dirty = false;
+  return NLC_OK;
+}
+
+extern "C" int nlc_destroy(nlc_ctx* x) {
+  if (!x) return NLC_OK;
+  cudaDeviceSynchronize();
+  cudaFree(x->d_w);
+  cudaFree(x->d_simt);
+  cudaFree(x->d_umma);
+  cudaFree(x->d_bias);
+  cudaFree(x->d_hash);
+  cudaFree(x->d_status);
+  cudaFree(x->d_m);
+  cudaFree(x->d_v);
+  cudaFree(x->d_grad);
+  cudaFree(x->d_loss);
+  cudaFree(x->ws);
+  delete x;
+  return NLC_OK;
+}
+
+extern "C" int nlc_create(const nlc_model_cfg* cfg, const float* h_w, size_t n, nlc_ctx** out) {
+  if (!out) return fail(NLC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg_ok(cfg))
+    return fail(NLC_ERR_UNSUPPORTED,
+                "unsupported configuration (h 1..3, C in {16,32,48,64}, n_res 0..4, K 1..16, "
+                "precision 0/1)");
+  if (!h_w || n != nlc_num_weights(cfg))
+    return fail(NLC_ERR_ARG, "expected %zu weights, got %zu", nlc_num_weights(cfg), n);
+  nlc_ctx* x = new nlc_ctx();
+  x->d = make_dims(cfg);
+  x->n_w = n;
+  int rc = NLC_OK;
+  do {
+    cudaError_t e;
+#define TRY_ALLOC(p, bytes)                                                             \
+  if ((e = cudaMalloc((void**)&(p), (bytes))) != cudaSuccess) {                         \
+    rc = fail(NLC_ERR_CUDA, "cudaMalloc failed: %s", cudaGetErrorString(e));            \
+    break;                                                                              \
+  }
+    if ((e = cudaGetDevice(&x->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, x->device)) !=
+            cudaSuccess) {
+      rc = fail(NLC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+      break;
+    }
+    TRY_ALLOC(x->d_w, n * 4);
+    TRY_ALLOC(x->d_simt, simt_floats(x->d) * 4);
+    TRY_ALLOC(x->d_umma, umma_halves(x->d) * 2);
+    TRY_ALLOC(x->d_bias, bias_floats(x->d) * 4);
+    TRY_ALLOC(x->d_hash, 8);
+    TRY_ALLOC(x->d_status, 4);
+    TRY_ALLOC(x->d_m, n * 4);
+    TRY_ALLOC(x->d_v, n * 4);
+    TRY_ALLOC(x->d_grad, n * 4);
+    TRY_ALLOC(x->d_loss, 8);
+    if ((e = cudaMemcpy(x->d_w, h_w, n * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(x->d_status, 0, 4)) != cudaSuccess ||
+        (e = cudaMemset(x->d_m, 0, n * 4)) != cudaSuccess ||
+        (e = cudaMemset(x->d_v, 0, n * 4)) != cudaSuccess) {
+      rc = fail(NLC_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    rc = ensure_packed(x, 0);
+    if (rc) break;
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+      rc = fail(NLC_ERR_CUDA, "weight packing failed: %s", cudaGetErrorString(e));
+      break;
+    }
+#undef TRY_ALLOC
+  } while (0);
+  if (rc != NLC_OK) {
+    nlc_destroy(x);
+    return rc;
+  }
+  *out = x;
+  return NLC_OK;
+}
+
+extern "C" int nlc_get_weights(nlc_ctx* x, float* h_w, size_t n) {
+  if (!x || !h_w || n != x->n_w) return fail(NLC_ERR_ARG, "bad arguments");
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(h_w, x->d_w, n * 4, cudaMemcpyDeviceToHost));
+  return NLC_OK;
+}
+
+extern "C" int nlc_set_weights(nlc_ctx* x, const float* h_w, size_t n) {
+  if (!x || !h_w || n != x->n_w) return fail(NLC_ERR_ARG, "bad arguments");
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(x->d_w, h_w, n * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(x->d_m, 0, n * 4));
+  CUDA_TRY(cudaMemset(x->d_v, 0, n * 4));
+  x->adam_t = 0;
+  x->dirty = true;
+  int rc = ensure_packed(x, 0);
+  if (rc) return rc;
+  CUDA_TRY(cudaDeviceSynchronize());
+  return NLC_OK;
+}
+
+extern "C" int nlc_weight_hash(nlc_ctx* x, uint64_t* h) {
+  if (!x || !h) return fail(NLC_ERR_ARG, "bad arguments");
+  int rc = ensure_packed(x, 0);
+  if (rc) return rc;
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(h, x->d_hash, 8, cudaMemcpyDeviceToHost));
+  return NLC_OK;
+}
+
+extern "C" int nlc_sync_status(nlc_ctx* x, nlc_stream stream) {
+  if (!x) return fail(NLC_ERR_ARG, "ctx is NULL");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int st = 0;
+  CUDA_TRY(cudaMemcpy(&st, x->d_status, 4, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(x->d_status, 0, 4));
+  switch (st) {
+    case 0: return NLC_OK;
+    case ST_CAPACITY: return fail(NLC_ERR_CAPACITY, "output capacity exceeded");
+    case ST_CORRUPT: return fail(NLC_ERR_CORRUPT, "corrupt container or stream");
+    case ST_WEIGHTS: return fail(NLC_ERR_WEIGHTS, "container made with other weights or precision");
+    case ST_TIMEOUT: return fail(NLC_ERR_TIMEOUT, "a bounded device wait timed out");
+    default: return fail(st, "device status %d", st);
+  }
+}
+
+extern "C" int nlc_set_tuning(nlc_ctx* x, int px_per_cta, int max_ctas) {
+  if (!x || px_per_cta < 1 || max_ctas < 0) return fail(NLC_ERR_ARG, "bad arguments");
+  x->px_per_cta = px_per_cta;
+  x->max_ctas = max_ctas;
+  return NLC_OK;
+}
+
+// ---------------------------------------------------------------------
+// Batch planning
+// ---------------------------------------------------------------------
+struct Batch {
+  std::vector<Unit> units;
+  std::vector<ImageRec> images;
+  long long n_px = 0;
+  int n_streams = 0;
+  long long T = 0;        // decode steps
+  long long max_front = 0;
+};
+
+static int plan_batch(const Dims& d, int n, uint8_t* const* ptrs, const int32_t* H,
+                      const int32_t* W, int patch, int layout, int sched_mode, Batch& b) {
+  b.units.clear();
+  b.images.clear();
+  b.n_px = 0;
+  b.n_streams = 0;
+  b.T = 0;
+  b.max_front = 0;
+  const int o = d.h + 1;
+  for (int i = 0; i < n; i++) {
+    const long long img_px_base = b.n_px;
+    ImageRec I;
+    I.H = H[i];
+    I.W = W[i];
+    I.stream_base = b.n_streams;
+    I.unit_base = (int)b.units.size();
+    I.n_units = 0;
+    long long img_start = 0;
+    const bool empty = H[i] == 0 || W[i] == 0;
+    const int P = patch > 0 ? patch : std::max(H[i], W[i]);
+    if (!empty) {
+      for (int y = 0; y < H[i]; y += P)
+        for (int xx = 0; xx < W[i]; xx += P) {
+          Unit u;
+          u.img = ptrs[i];
+          u.px_base = b.n_px;
+          u.img_W = W[i];
+          u.y0 = y;
+          u.x0 = xx;
+          u.Hu = std::min(P, H[i] - y);
+          u.Wu = std::min(P, W[i] - xx);
+          u.stream_base = b.n_streams;
+          u.image = i;
+          u.pad_ = 0;
+          u.img_px_base = img_px_base;
+          long long Tu;
+          if (sched_mode == NLC_SCHED_WAVEFRONT) {
+            u.start_step = 0;
+            Tu = u.Wu + (long long)(u.Hu - 1) * o;
+            b.max_front += std::min<long long>(u.Hu, (u.Wu + o - 1) / o);
+          } else if (sched_mode == NLC_SCHED_RASTER) {
+            u.start_step = 0;
+            Tu = (long long)u.Hu * u.Wu;
+            b.max_front += 1;
+          } else {
+            if (img_start > INT32_MAX) return fail(NLC_ERR_UNSUPPORTED, "image too large");
+            u.start_step = (int)img_start;
+            Tu = (long long)u.Hu * u.Wu;
+            img_start += Tu;
+          }
+          b.T = std::max(b.T, (long long)u.start_step + Tu);
+          b.n_px += (long long)u.Hu * u.Wu;
+          b.n_streams += layout == NLC_LAYOUT_ROW ? u.Hu : 1;
+          b.units.push_back(u);
+          I.n_units++;
+        }
+      if (sched_mode == NLC_SCHED_SEQUENTIAL) b.max_front += 1;
+    }
+    I.n_streams = b.n_streams - I.stream_base;
+    b.images.push_back(I);
+  }
+  if (b.T > INT32_MAX || b.n_px > (1LL << 40))
+    return fail(NLC_ERR_UNSUPPORTED, "batch too large");
+  return NLC_OK;
+}
+
+static int check_images(int n, const int32_t* H, const int32_t* W, const void* const* data,
+                        int patch) {
+  if (n < 0) return fail(NLC_ERR_ARG, "n < 0");
+  if (patch < 0) return fail(NLC_ERR_ARG, "patch < 0");
+  for (int i = 0; i < n; i++) {
+    if (H[i] < 0 || W[i] < 0) return fail(NLC_ERR_ARG, "image %d has a negative size", i);
+    if ((long long)H[i] * W[i] > 0 && !data[i])
+      return fail(NLC_ERR_ARG, "image %d has no data pointer", i);
+    if ((long long)H[i] * W[i] > (1LL << 31)) return fail(NLC_ERR_UNSUPPORTED, "image too large");
+  }
+  return NLC_OK;
+}
+
+// Workspace arena (256-byte aligned pieces).
+struct Arena {
+  unsigned char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += (count * sizeof(T) + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+static int ensure_ws(nlc_ctx* x, size_t bytes) {
+  if (bytes <= x->ws_cap) return NLC_OK;
+  CUDA_TRY(cudaDeviceSynchronize());
+  cudaFree(x->ws);
+  x->ws = nullptr;
+  x->ws_cap = 0;
+  size_t cap = std::max(bytes, x->ws_cap * 2);
+  CUDA_TRY(cudaMalloc((void**)&x->ws, cap));
+  x->ws_cap = cap;
+  return NLC_OK;
+}
+
+// Lays out the per-call buffers; with base == nullptr only measures.
+static size_t layout_bufs(const Batch& b, unsigned char* base, CodecBufs& cb, int* status,
+                          bool encode) {
+  Arena a{base};
+  const size_t U = b.units.size(), S = (size_t)b.n_streams;
+  cb.units = a.take<Unit>(U + 1);
+  cb.images = a.take<ImageRec>(b.images.size() + 1);
+  cb.n_units = (int)U;
+  cb.n_images = (int)b.images.size();
+  cb.n_streams = (int)S;
+  cb.n_px = b.n_px;
+  cb.lens = a.take<int32_t>(S + 1);
+  cb.unit_bytes = a.take<unsigned long long>(U + 1 + (b.images.size() + 1) / 2 + 1);
+  cb.unit_off = a.take<unsigned long long>(U + 1);
+  cb.st_pos = a.take<unsigned long long>(S + 1);
+  cb.st_x = a.take<uint32_t>(S + 1);
+  cb.st_end = a.take<unsigned long long>(S + 1);
+  cb.bar = a.take<unsigned>(64);
+  if (encode) {
+    cb.stage = a.take<uint32_t>(3 * (size_t)b.n_px + 1);
+    cb.scratch = a.take<uint8_t>(6 * (size_t)b.n_px + 4 * S + 16);
+  } else {
+    cb.stage = nullptr;
+    cb.scratch = nullptr;
+  }
+  cb.status = status;
+  return a.off;
+}
+
+static int upload_batch(const Batch& b, CodecBufs& cb, cudaStream_t s) {
+  if (!b.units.empty())
+    CUDA_TRY(cudaMemcpyAsync((void*)cb.units, b.units.data(), b.units.size() * sizeof(Unit),
+                             cudaMemcpyHostToDevice, s));
+  if (!b.images.empty())
+    CUDA_TRY(cudaMemcpyAsync((void*)cb.images, b.images.data(), b.images.size() * sizeof(ImageRec),
+                             cudaMemcpyHostToDevice, s));
+  return NLC_OK;
+}
+
+extern "C" int nlc_compress_bound(const int32_t* H, const int32_t* W, int n, int patch, int layout,
+                                  size_t* bytes) {
+  if (!bytes || (n > 0 && (!H || !W)) || n < 0 || patch < 0 || (layout != 0 && layout != 1))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  size_t tot = 0;
+  for (int i = 0; i < n; i++) {
+    if (H[i] < 0 || W[i] < 0) return fail(NLC_ERR_ARG, "negative image size");
+    size_t ns = 0;
+    if (H[i] > 0 && W[i] > 0) {
+      const int P = patch > 0 ? patch : std::max(H[i], W[i]);
+      const size_t nu = (size_t)((H[i] + P - 1) / P) * ((W[i] + P - 1) / P);
+      ns = layout == 1 ? (size_t)((W[i] + P - 1) / P) * H[i] : nu;
+    }
+    size_t c = kHeaderBytes + 8 * ns + 6 * (size_t)H[i] * W[i];
+    tot += (c + 15) & ~(size_t)15;
+  }
+  *bytes = tot;
+  return NLC_OK;
+}
+
+extern "C" int nlc_compress(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch, int layout,
+                            uint8_t* d_out, size_t cap, uint64_t* d_offsets, nlc_stream stream) {
+  if (!x || (n > 0 && !imgs) || !d_offsets || (layout != 0 && layout != 1))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  std::vector<int32_t> H(n), W(n);
+  std::vector<const void*> data(n);
+  std::vector<uint8_t*> ptrs(n);
+  for (int i = 0; i < n; i++) {
+    H[i] = imgs[i].H;
+    W[i] = imgs[i].W;
+    data[i] = imgs[i].data;
+    ptrs[i] = const_cast<uint8_t*>(imgs[i].data);
+  }
+  int rc = check_images(n, H.data(), W.data(), data.data(), patch);
+  if (rc) return rc;
+  if (!d_out && cap > 0) return fail(NLC_ERR_ARG, "d_out is NULL");
+  Batch b;
+  rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, layout, NLC_SCHED_RASTER, b);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CodecBufs cb;
+  size_t need = layout_bufs(b, nullptr, cb, x->d_status, true);
+  if ((rc = ensure_ws(x, need))) return rc;
+  layout_bufs(b, x->ws, cb, x->d_status, true);
+  if ((rc = ensure_packed(x, s))) return rc;
+  if ((rc = upload_batch(b, cb, s))) return rc;
+  CUDA_TRY(launch_encode(model_view(x), cb, layout, patch, d_out, (unsigned long long)cap,
+                         reinterpret_cast<unsigned long long*>(d_offsets), x->sm_count, s));
+  return NLC_OK;
+}
+
+extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d_offsets,
+                              const nlc_image_out* outs, int n, int patch, int layout,
+                              int schedule, nlc_stream stream) {
+  if (!x || (n > 0 && (!outs || !d_in || !d_offsets)) || (layout != 0 && layout != 1))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  if (schedule < 0 || schedule > 2) return fail(NLC_ERR_ARG, "unknown schedule %d", schedule);
+  if (layout == NLC_LAYOUT_UNIT && schedule == NLC_SCHED_WAVEFRONT)
+    return fail(NLC_ERR_ARG, "one stream per unit can only be decoded in raster order");
+  std::vector<int32_t> H(n), W(n);
+  std::vector<const void*> data(n);
+  std::vector<uint8_t*> ptrs(n);
+  for (int i = 0; i < n; i++) {
+    H[i] = outs[i].H;
+    W[i] = outs[i].W;
+    data[i] = outs[i].data;
+    ptrs[i] = outs[i].data;
+  }
+  int rc = check_images(n, H.data(), W.data(), data.data(), patch);
+  if (rc) return rc;
+  Batch b;
+  rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, layout, schedule, b);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const DeviceModel m = model_view(x);
+  if (decode_smem_bytes(x->d, (int)b.units.size()) > 227 * 1024)
+    return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
+  CodecBufs cb;
+  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false);
+  if ((rc = ensure_ws(x, need))) return rc;
+  layout_bufs(b, x->ws, cb, x->d_status, false);
+  if ((rc = ensure_packed(x, s))) return rc;
+  if ((rc = upload_batch(b, cb, s))) return rc;
+  int gmax = decode_max_grid(m, (int)b.units.size(), x->sm_count);
+  if (gmax < 1) return fail(NLC_ERR_UNSUPPORTED, "decoder does not fit on an SM");
+  if (x->max_ctas > 0) gmax = std::min(gmax, x->max_ctas);
+  long long g = (b.max_front + x->px_per_cta - 1) / x->px_per_cta;
+  int grid = (int)std::max(1LL, std::min<long long>(g, gmax));
+  // the barrier's arrival counter reaches grid * T; keep it within 32 bits
+  if ((long long)grid * b.T >= (1LL << 32) - 1) grid = 1;
+  const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
+  CUDA_TRY(launch_decode(m, cb, d_in, reinterpret_cast<const unsigned long long*>(d_offsets),
+                         layout, patch, sched, (int)b.T, grid, s));
+  return NLC_OK;
+}
+
+extern "C" int nlc_forward(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch, float* d_params,
+                           float* d_bits, nlc_stream stream) {
+  if (!x || (n > 0 && !imgs)) return fail(NLC_ERR_ARG, "bad arguments");
+  std::vector<int32_t> H(n), W(n);
+  std::vector<const void*> data(n);
+  std::vector<uint8_t*> ptrs(n);
+  for (int i = 0; i < n; i++) {
+    H[i] = imgs[i].H;
+    W[i] = imgs[i].W;
+    data[i] = imgs[i].data;
+    ptrs[i] = const_cast<uint8_t*>(imgs[i].data);
+  }
+  int rc = check_images(n, H.data(), W.data(), data.data(), patch);
+  if (rc) return rc;
+  Batch b;
+  rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, 1, NLC_SCHED_RASTER, b);
+  if (rc) return rc;
+  if (b.n_px > 0 && !d_params && !d_bits) return NLC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  CodecBufs cb;
+  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false);
+  if ((rc = ensure_ws(x, need))) return rc;
+  layout_bufs(b, x->ws, cb, x->d_status, false);
+  if ((rc = ensure_packed(x, s))) return rc;
+  if ((rc = upload_batch(b, cb, s))) return rc;
+  CUDA_TRY(launch_forward(model_view(x), cb, d_params, d_bits, x->sm_count, s));
+  return NLC_OK;
+}
+
+extern "C" int nlc_tables(nlc_ctx* x, const float* d_params, const uint8_t* d_pixels, int64_t n,
+                          uint32_t* d_cum, nlc_stream stream) {
+  if (!x || n < 0 || (n > 0 && (!d_params || !d_pixels || !d_cum)))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  CUDA_TRY(launch_tables(model_view(x), d_params, d_pixels, n, d_cum, (cudaStream_t)stream));
+  return NLC_OK;
+}
+
+extern "C" int nlc_rans_encode(const uint32_t* d_start, const uint32_t* d_freq,
+                               const int64_t* d_sym_off, int n_streams, uint8_t* d_bytes,
+                               int64_t stride, int32_t* d_len, nlc_stream stream) {
+  if (n_streams < 0 || (n_streams > 0 && (!d_start || !d_freq || !d_sym_off || !d_bytes ||
+                                          !d_len || stride < 4)))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  CUDA_TRY(launch_rans_encode(d_start, d_freq, reinterpret_cast<const long long*>(d_sym_off),
+                              n_streams, d_bytes, stride, d_len, (cudaStream_t)stream));
+  return NLC_OK;
+}
+
+extern "C" int nlc_rans_decode(nlc_ctx* x, const uint8_t* d_bytes, int64_t stride,
+                               const int32_t* d_len, const uint32_t* d_cum,
+                               const int64_t* d_sym_off, int n_streams, int32_t* d_sym,
+                               nlc_stream stream) {
+  if (!x || n_streams < 0 ||
+      (n_streams > 0 && (!d_bytes || !d_len || !d_cum || !d_sym_off || !d_sym || stride < 4)))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  CUDA_TRY(launch_rans_decode(d_bytes, stride, d_len, d_cum,
+                              reinterpret_cast<const long long*>(d_sym_off), n_streams, d_sym,
+                              x->d_status, (cudaStream_t)stream));
+  return NLC_OK;
+}
+
+// ---------------------------------------------------------------------
+// Training
+// ---------------------------------------------------------------------
+extern "C" int nlc_loss_grad(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W,
+                             float* d_loss, float* d_grad, nlc_stream stream) {
+  if (!x || N < 1 || H < 1 || W < 1 || !d_batch || !d_loss || !d_grad)
+    return fail(NLC_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long npx = (long long)N * H * W;
+  const size_t need = train_ws_bytes(x->d, npx, x->sm_count);
+  int rc = ensure_ws(x, need);
+  if (rc) return rc;
+  if ((rc = ensure_packed(x, s))) return rc;
+  CUDA_TRY(launch_loss_grad(x->d, x->d_w, x->d_simt, d_batch, N, H, W, d_loss, d_grad, x->ws,
+                            x->sm_count, s));
+  return NLC_OK;
+}
+
+extern "C" int nlc_train_step(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W, float lr,
+                              float* h_loss, nlc_stream stream) {
+  if (!x || N < 1 || H < 1 || W < 1 || !d_batch || !(lr > 0.f))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = nlc_loss_grad(x, d_batch, N, H, W, x->d_loss, x->d_grad, stream);
+  if (rc) return rc;
+  x->adam_t += 1;
+  CUDA_TRY(launch_adam(x->d_w, x->d_grad, x->d_m, x->d_v, (int)x->n_w, lr, 0.9f, 0.999f, 1e-8f,
+                       x->adam_t, s));
+  x->dirty = true;
+  if (h_loss) {
+    CUDA_TRY(cudaMemcpyAsync(h_loss, x->d_loss, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return NLC_OK;
+}

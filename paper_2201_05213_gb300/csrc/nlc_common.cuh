@@ -1,0 +1,175 @@
+// Shared device-side definitions of the nlc CUDA library (sm_103a).
+//
+// Everything that decides a frequency table is written with explicitly
+// rounded intrinsics and the library is compiled with -fmad=false, so the
+// table of a pixel is a pure function of its inputs: the encoder (all pixels
+// in parallel) and the decoder (one wavefront per step) compute identical
+// tables, which the rANS round trip requires (Section 4: the paper reuses
+// the decoder's inference in the encoder for the same reason).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nlc {
+
+constexpr uint32_t kRansL = 1u << 23;   // rANS state interval [2^23, 2^31)
+constexpr int kMq = 65280;              // 2^16 - 256 counts spread by the CDF
+constexpr int kMaxK = 16;               // mixture components
+constexpr int kMaxR = 4;                // residual blocks
+constexpr int kMaxH = 3;                // horizon
+constexpr int kMaxC = 64;               // channels of the local network
+constexpr int kThreads = 256;           // threads of the codec kernels
+constexpr int kWarps = kThreads / 32;
+
+enum Status {
+  ST_OK = 0,
+  ST_ARG = 1,
+  ST_CAPACITY = 2,
+  ST_CORRUPT = 3,
+  ST_WEIGHTS = 4,
+  ST_CUDA = 5,
+  ST_TIMEOUT = 6,
+  ST_UNSUPPORTED = 7,
+};
+
+enum Precision { PREC_FP32 = 0, PREC_BF16 = 1 };
+enum Schedule { SCHED_RASTER = 0, SCHED_WAVEFRONT = 1 };
+
+// Model dimensions.  F = 6h(h+1) context features (2h(h+1) pixels x RGB),
+// Fp = F rounded up to a multiple of 16, NO = 10K network outputs, NOp = NO
+// rounded up to a multiple of 16, ldP = NOp + 4 (row stride of the per-pixel
+// outputs in shared memory, padded against bank conflicts).
+struct Dims {
+  int h, C, R, K;
+  int F, Fp, NO, NOp, ldP;
+  int prec;
+};
+
+// One coding unit (a whole image or one patch of it).
+struct Unit {
+  uint8_t* img;          // image base (decode: output; encode: input), HWC uint8
+  long long px_base;     // pixels of all preceding units of the batch
+  int img_W;             // image width (row stride = 3 * img_W bytes)
+  int y0, x0, Hu, Wu;    // unit origin and size inside its image
+  int stream_base;       // index of the unit's first rANS stream
+  int start_step;        // global step at which the unit's local step 0 runs
+  int image;             // image index in the batch
+  int pad_;
+  long long img_px_base; // pixels of all preceding images (raster output order)
+};
+
+// Byte offsets of the packed weight blobs inside the device weight buffer.
+struct WeightView {
+  const float* simt;            // FP32: W0T[F][C] b0[C] {W1T[C][C] b1 W2T[C][C] b2}xR WHT[C][NOp] bH[NOp]
+  const uint16_t* umma;         // BF16 UMMA tiles (see nlc_model.cuh)
+  const float* bias;            // BF16 path biases: b0[C] {b1 b2}xR bH[NOp]
+  int simt_floats;
+  int umma_halves;
+};
+
+__device__ __forceinline__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// Approximate 2^x and 1/x (PTX ex2.approx / rcp.approx): deterministic
+// single MUFU instructions.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint8_t ld_cg_u8(const uint8_t* p) {
+  unsigned short v;
+  asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(v) : "l"(p));
+  return (uint8_t)v;
+}
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch.  The arrival counter grows
+// monotonically (generation g completes at nblocks * g arrivals), so it
+// never needs a reset inside the launch.  The wait is bounded: after
+// kSpinLimit polls it records ST_TIMEOUT and returns false, and every CTA
+// then leaves its loop.
+constexpr unsigned kSpinLimit = 1u << 25;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
+                                             unsigned& my_gen, int* status, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned target = my_gen + 1;
+    __threadfence();
+    unsigned old = atomicAdd(count, 1u);
+    if (old == nblocks * target - 1u) {
+      st_release_gpu(gen, target);
+    } else {
+      unsigned it = 0;
+      while (ld_acquire_gpu(gen) < target) {
+        if (++it > kSpinLimit) {
+          set_status(status, ST_TIMEOUT);
+          *s_flag = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    my_gen = target;
+    if (ld_cg_u32((const uint32_t*)status) == ST_TIMEOUT) *s_flag = 1;
+  }
+  __syncthreads();
+  return *s_flag == 0;
+}
+
+// Front of a unit at its local step tau.
+//   wavefront (Section 3): rows i with j = tau - (h+1) i in [0, Wu)
+//   raster: the single pixel tau of the unit in raster order.
+struct Front {
+  int i_lo, n;  // first row and number of pixels
+};
+
+__device__ __forceinline__ Front unit_front(const Unit& u, int t, int h, int sched) {
+  Front f{0, 0};
+  int tau = t - u.start_step;
+  if (tau < 0) return f;
+  if (sched == SCHED_WAVEFRONT) {
+    int o = h + 1;
+    int hi = tau / o;
+    if (hi > u.Hu - 1) hi = u.Hu - 1;
+    int num = tau - u.Wu + 1;  // i >= ceil(num / o)
+    int lo = num <= 0 ? 0 : (num + o - 1) / o;
+    if (hi >= lo) { f.i_lo = lo; f.n = hi - lo + 1; }
+  } else {
+    if (tau < u.Hu * u.Wu) { f.i_lo = tau / u.Wu; f.n = 1; }
+  }
+  return f;
+}
+
+__device__ __forceinline__ int front_col(const Unit& u, int t, int i, int h, int sched) {
+  int tau = t - u.start_step;
+  return sched == SCHED_WAVEFRONT ? tau - (h + 1) * i : tau % u.Wu;
+}
+
+}  // namespace nlc

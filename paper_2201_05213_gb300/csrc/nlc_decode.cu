@@ -1,0 +1,160 @@
+// The wavefront decoder (Algorithm 1, Section 3) as one persistent
+// cooperative kernel, and its launcher.
+#include "nlc_tile.cuh"
+
+namespace nlc {
+
+// ---------------------------------------------------------------------
+// Decoder: persistent cooperative kernel.  Step t decodes, for every unit,
+// the pixels of its front (wavefront: j = tau - (h+1) i, Section 3; raster:
+// one pixel).  The step's pixels are split evenly across the CTAs; each CTA
+// runs gather -> network -> per-pixel CDF + rANS for its share, then all
+// CTAs meet at a grid barrier before step t+1.
+// ---------------------------------------------------------------------
+struct DecodeArgs {
+  DeviceModel m;
+  const Unit* units;
+  int n_units;
+  int layout, sched, T;
+  const uint8_t* in;
+  uint32_t* st_x;
+  unsigned long long* st_pos;
+  const unsigned long long* st_end;
+  unsigned* bar;
+  int* status;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Dims& d = a.m.d;
+  TileSmem t = carve(d, smem, a.n_units);
+  if constexpr (PREC == PREC_BF16) tc_setup(t.tc);
+  load_weights<PREC>(a.m, t);
+  if (threadIdx.x == 0) t.flag[0] = 0;
+  __syncthreads();
+  constexpr int MT = tile_size<PREC>();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int K = d.K, ldP = d.ldP, h = d.h;
+  unsigned my_gen = 0;
+  const unsigned G = gridDim.x;
+  for (int step = 0; step < a.T; step++) {
+    const int F = front_scan(a.units, a.n_units, step, h, a.sched, t.pre, t.sh);
+    const long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
+    for (long long base = lo; base < hi; base += MT) {
+      const int n = (int)min((long long)MT, hi - base);
+      for (int s = threadIdx.x; s < MT; s += blockDim.x) {
+        PixSlot ps{-1, 0, 0, 0};
+        if (s < n) {
+          const int q = (int)(base + s);
+          int lo2 = 0, hi2 = a.n_units - 1;  // last u with pre[u] <= q
+          while (lo2 < hi2) {
+            int mid = (lo2 + hi2 + 1) >> 1;
+            if (t.pre[mid] <= q) lo2 = mid; else hi2 = mid - 1;
+          }
+          const Unit U = a.units[lo2];
+          const Front fr = unit_front(U, step, h, a.sched);
+          ps.unit = lo2;
+          ps.i = fr.i_lo + (q - t.pre[lo2]);
+          ps.j = front_col(U, step, ps.i, h, a.sched);
+          ps.aux = U.stream_base + (a.layout == 1 ? ps.i : 0);
+        }
+        t.slots[s] = ps;
+      }
+      __syncthreads();
+      tile_network<PREC, true>(a.m, a.units, t);
+      for (int s = warp; s < n; s += kWarps) {
+        const PixSlot ps = t.slots[s];
+        const Unit U = a.units[ps.unit];
+        const int sid = ps.aux;
+        WarpRansDec dec;
+        dec.x = ld_cg_u32(a.st_x + sid);
+        dec.pos = ld_cg_u64(a.st_pos + sid);
+        dec.end = a.st_end[sid];
+        dec.bad = false;
+        dec.prefetch(a.in, lane);
+        CompState cs;
+        comp_init(t.U0 + (size_t)s * ldP, K, lane, cs);
+        int v[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ch++) {
+          float mloc = channel_table(cs, K, ch, v[0], v[1], lane, t.ws[warp]);
+          v[ch] = dec.decode(t.ws[warp], lane);
+          if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], lane);
+          __syncwarp();
+        }
+        if (lane == 0) {
+          uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
+          px[0] = (uint8_t)v[0];
+          px[1] = (uint8_t)v[1];
+          px[2] = (uint8_t)v[2];
+          const unsigned long long np = dec.pos + (unsigned long long)dec.used;
+          a.st_x[sid] = dec.x;
+          a.st_pos[sid] = np;
+          const bool last = a.layout == 1 ? (ps.j == U.Wu - 1)
+                                          : (ps.i == U.Hu - 1 && ps.j == U.Wu - 1);
+          if (dec.bad || (last && (dec.x != kRansL || np != dec.end)))
+            set_status(a.status, ST_CORRUPT);
+        }
+      }
+      __syncthreads();
+    }
+    if (G > 1) {
+      if (!grid_barrier(a.bar, a.bar + 1, G, my_gen, a.status, t.flag)) break;
+    } else {
+      __syncthreads();
+    }
+  }
+  if constexpr (PREC == PREC_BF16) tc_teardown(t.tc);
+}
+
+size_t decode_smem_bytes(const Dims& d, int n_units) { return tile_smem_bytes(d, n_units); }
+
+static const void* decode_fn(int prec) {
+  return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16>
+                           : (const void*)decode_kernel<PREC_FP32>;
+}
+
+int decode_max_grid(const DeviceModel& m, int n_units, int sm_count) {
+  const size_t smem = decode_smem_bytes(m.d, n_units);
+  const void* fn = decode_fn(m.d.prec);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem) != cudaSuccess)
+    return 0;
+  return per * sm_count;
+}
+
+cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
+                          const unsigned long long* d_offsets, int layout, int patch, int sched,
+                          int T, int grid, cudaStream_t s) {
+  cudaError_t e;
+  if (b.n_images == 0) return cudaSuccess;
+  if ((e = launch_parse(m, b, in, d_offsets, layout, patch, s)) != cudaSuccess) return e;
+  if (b.n_units == 0) return cudaSuccess;
+  if ((e = cudaMemsetAsync(b.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+  DecodeArgs a;
+  a.m = m;
+  a.units = b.units;
+  a.n_units = b.n_units;
+  a.layout = layout;
+  a.sched = sched;
+  a.T = T;
+  a.in = in;
+  a.st_x = b.st_x;
+  a.st_pos = b.st_pos;
+  a.st_end = b.st_end;
+  a.bar = b.bar;
+  a.status = b.status;
+  const size_t smem = decode_smem_bytes(m.d, b.n_units);
+  const void* fn = decode_fn(m.d.prec);
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  void* args[] = {&a};
+  if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(1), dim3(kThreads), args, smem, s);
+}
+
+}  // namespace nlc

@@ -1,0 +1,80 @@
+// Host-visible declarations of the kernels' launchers (internal to the
+// library; the public surface is include/nlc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nlc_common.cuh"
+
+namespace nlc {
+
+// Per-image record of a batch.
+struct ImageRec {
+  int H, W;
+  int stream_base, n_streams;
+  int unit_base, n_units;
+};
+
+// Container header (32 bytes, little endian), followed by n_streams uint32
+// stream lengths in bytes, then the streams back to back; the container is
+// zero-padded to a multiple of 16 bytes.
+constexpr uint32_t kMagic = 0x31434C4Eu;  // "NLC1"
+constexpr int kVersion = 1;
+constexpr int kHeaderBytes = 32;
+
+struct DeviceModel {
+  Dims d;
+  WeightView w;
+  const unsigned long long* hash;
+};
+
+// Per-call device buffers (sub-allocated from the context workspace).
+struct CodecBufs {
+  const Unit* units;
+  const ImageRec* images;
+  int n_units, n_images, n_streams;
+  long long n_px;
+  // encoder
+  uint32_t* stage;               // 3 * n_px packed (start | freq << 16)
+  uint8_t* scratch;              // per-stream byte slots
+  int32_t* lens;                 // n_streams
+  unsigned long long* unit_bytes;  // n_units
+  unsigned long long* unit_off;    // n_units (absolute byte offset of the unit's first stream)
+  // decoder
+  uint32_t* st_x;
+  unsigned long long* st_pos;
+  unsigned long long* st_end;
+  unsigned* bar;                 // 2 words: arrivals, generation
+  int* status;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_repack(const Dims& d, const float* w, float* simt, uint16_t* umma, float* bias,
+                          unsigned long long* hash, int n_w, cudaStream_t s);
+
+cudaError_t launch_encode(const DeviceModel& m, const CodecBufs& b, int layout, int patch,
+                          uint8_t* out, unsigned long long cap, unsigned long long* d_offsets,
+                          int sm_count, cudaStream_t s);
+cudaError_t launch_enc_tables(const DeviceModel& m, const CodecBufs& b, int sm_count,
+                              cudaStream_t s);
+cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
+                         const unsigned long long* d_offsets, int layout, int patch,
+                         cudaStream_t s);
+cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
+                          const unsigned long long* d_offsets, int layout, int patch, int sched,
+                          int T, int grid, cudaStream_t s);
+int decode_max_grid(const DeviceModel& m, int n_units, int sm_count);
+size_t decode_smem_bytes(const Dims& d, int n_units);
+cudaError_t launch_forward(const DeviceModel& m, const CodecBufs& b, float* params, float* bits,
+                           int sm_count, cudaStream_t s);
+cudaError_t launch_tables(const DeviceModel& m, const float* params, const uint8_t* pixels,
+                          long long n, uint32_t* cum, cudaStream_t s);
+cudaError_t launch_rans_encode(const uint32_t* start, const uint32_t* freq,
+                               const long long* sym_off, int n_streams, uint8_t* out,
+                               long long stride, int32_t* lens, cudaStream_t s);
+cudaError_t launch_rans_decode(const uint8_t* in, long long stride, const int32_t* lens,
+                               const uint32_t* cum, const long long* sym_off, int n_streams,
+                               int32_t* sym, int* status, cudaStream_t s);
+
+}  // namespace nlc

@@ -1,0 +1,358 @@
+// Per-tile pipeline of the local autoregressive model (device code):
+//   gather of the causal context (Eq. 3) -> local network (Section 2.1) ->
+//   discretized logistic mixture -> CDF -> 16-bit frequency table.
+// Used by the decoder (one wavefront step per tile) and by the encoder (any
+// pixels per tile); the arithmetic per pixel is independent of the tile
+// position, so both produce identical tables.
+#pragma once
+
+#include "nlc_common.cuh"
+
+namespace nlc {
+
+// One pixel slot of a tile.
+struct PixSlot {
+  int unit;   // unit index, -1 for an empty slot
+  int i, j;   // position inside the unit
+  int aux;    // decoder: stream index; encoder: pixel index in the batch
+};
+
+// ---------------------------------------------------------------------
+// Context gather (Eq. 3): taps p enumerate rows dy=-h..-1 with dx=-h..h,
+// then dy=0 with dx=-h..-1; feature 3p+c holds channel c.  Outside the
+// unit the network input is zero.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ void tap_offset(int p, int h, int& dy, int& dx) {
+  int w = 2 * h + 1;
+  dy = p / w - h;
+  dx = p % w - h;
+}
+
+// FP32 layout: X[f][m] (feature-major), value (2v-255)/255.
+template <int MT, bool kCoherent>
+__device__ void gather_f32(const Unit* units, const PixSlot* slots, int h, float* X) {
+  const int ntap = 2 * h * (h + 1);
+  for (int it = threadIdx.x; it < MT * ntap; it += blockDim.x) {
+    int m = it % MT, p = it / MT;
+    const PixSlot s = slots[m];
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    if (s.unit >= 0) {
+      const Unit u = units[s.unit];
+      int dy, dx;
+      tap_offset(p, h, dy, dx);
+      int ii = s.i + dy, jj = s.j + dx;
+      if (ii >= 0 && ii < u.Hu && jj >= 0 && jj < u.Wu) {
+        const uint8_t* px = u.img + ((long long)(u.y0 + ii) * u.img_W + (u.x0 + jj)) * 3;
+        int a, b, c;
+        if (kCoherent) { a = ld_cg_u8(px); b = ld_cg_u8(px + 1); c = ld_cg_u8(px + 2); }
+        else { a = px[0]; b = px[1]; c = px[2]; }
+        v0 = __fdiv_rn((float)(2 * a - 255), 255.f);
+        v1 = __fdiv_rn((float)(2 * b - 255), 255.f);
+        v2 = __fdiv_rn((float)(2 * c - 255), 255.f);
+      }
+    }
+    X[(3 * p + 0) * MT + m] = v0;
+    X[(3 * p + 1) * MT + m] = v1;
+    X[(3 * p + 2) * MT + m] = v2;
+  }
+}
+
+__device__ __forceinline__ float elu_f(float x) { return x > 0.f ? x : expm1f(x); }
+
+// ---------------------------------------------------------------------
+// FP32 SIMT local network.  Activations are feature-major [n][m]; each
+// thread owns 4 pixels x NB outputs (N = 16 NB), accumulating over k in
+// ascending order with explicit fma.
+// ---------------------------------------------------------------------
+enum GemmMode { GM_STORE = 0, GM_ELU = 1, GM_RESID = 2, GM_HEAD = 3 };
+
+template <int MT, int NB, int MODE>
+__device__ __noinline__ void gemm_simt(const float* __restrict__ in, int Kd,
+                                          const float* __restrict__ WT,
+                                          const float* __restrict__ bias, float* __restrict__ out,
+                                          int ldp) {
+  static_assert(MT == 64, "the SIMT tile is 64 pixels");
+  constexpr int N = 16 * NB;
+  const int tm = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  const int m0 = tm * 4, n0 = tn * NB;
+  float acc[4][NB];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < NB; b++) acc[a][b] = 0.f;
+  for (int k = 0; k < Kd; k++) {
+    const float4 x = *reinterpret_cast<const float4*>(in + k * MT + m0);
+    const float* wr = WT + k * N + n0;
+    float wv[NB];
+#pragma unroll
+    for (int b = 0; b < NB; b++) wv[b] = wr[b];
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+      acc[0][b] = __fmaf_rn(x.x, wv[b], acc[0][b]);
+      acc[1][b] = __fmaf_rn(x.y, wv[b], acc[1][b]);
+      acc[2][b] = __fmaf_rn(x.z, wv[b], acc[2][b]);
+      acc[3][b] = __fmaf_rn(x.w, wv[b], acc[3][b]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; b++) {
+    const float bb = bias[n0 + b];
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      float v = __fadd_rn(acc[a][b], bb);
+      if (MODE == GM_STORE) out[(n0 + b) * MT + m0 + a] = v;
+      if (MODE == GM_ELU) out[(n0 + b) * MT + m0 + a] = elu_f(v);
+      if (MODE == GM_RESID) {
+        float* o = out + (n0 + b) * MT + m0 + a;
+        *o = __fadd_rn(*o, v);
+      }
+      if (MODE == GM_HEAD) out[(m0 + a) * ldp + n0 + b] = v;
+    }
+  }
+}
+
+template <int MT, int NB>
+__device__ __forceinline__ void gemm_layer(int mode, const float* in, int Kd, const float* WT,
+                                           const float* bias, float* out, int ldp) {
+  switch (mode) {
+    case GM_STORE: gemm_simt<MT, NB, GM_STORE>(in, Kd, WT, bias, out, ldp); break;
+    case GM_ELU: gemm_simt<MT, NB, GM_ELU>(in, Kd, WT, bias, out, ldp); break;
+    case GM_RESID: gemm_simt<MT, NB, GM_RESID>(in, Kd, WT, bias, out, ldp); break;
+    default: gemm_simt<MT, NB, GM_HEAD>(in, Kd, WT, bias, out, ldp); break;
+  }
+}
+
+template <int MT>
+__device__ void gemm_dispatch(int mode, const float* in, int Kd, const float* WT, const float* bias,
+                              int N, float* out, int ldp) {
+  switch (N / 16) {
+    case 1: gemm_layer<MT, 1>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 2: gemm_layer<MT, 2>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 3: gemm_layer<MT, 3>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 4: gemm_layer<MT, 4>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 5: gemm_layer<MT, 5>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 6: gemm_layer<MT, 6>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 7: gemm_layer<MT, 7>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 8: gemm_layer<MT, 8>(mode, in, Kd, WT, bias, out, ldp); break;
+    case 9: gemm_layer<MT, 9>(mode, in, Kd, WT, bias, out, ldp); break;
+    default: gemm_layer<MT, 10>(mode, in, Kd, WT, bias, out, ldp); break;
+  }
+}
+
+// Floats of the packed FP32 weights:
+// W0T[F][C] b0[C] {W1T[C][C] b1[C] W2T[C][C] b2[C]} x R WHT[C][NOp] bH[NOp].
+__host__ __device__ inline size_t simt_floats(const Dims& d) {
+  return (size_t)d.F * d.C + d.C + (size_t)d.R * (2 * d.C * d.C + 2 * d.C) + (size_t)d.C * d.NOp +
+         d.NOp;
+}
+
+// Shared-memory plan of the FP32 tile pipeline (all offsets in floats).
+struct SimtPlan {
+  int w_off, a_off, b1_off, u0_off, end;
+};
+
+__host__ __device__ inline SimtPlan simt_plan(const Dims& d, int simt_floats, int MT) {
+  SimtPlan p;
+  int u0 = d.Fp * MT;
+  if (d.C * MT > u0) u0 = d.C * MT;
+  if (MT * d.ldP > u0) u0 = MT * d.ldP;
+  p.w_off = 0;
+  p.a_off = (simt_floats + 3) & ~3;
+  p.b1_off = p.a_off + d.C * MT;
+  p.u0_off = p.b1_off + d.C * MT;
+  p.end = p.u0_off + u0;
+  return p;
+}
+
+// Network of a 64-pixel tile: X (features, in U0) -> P[m][ldP] (in U0).
+template <int MT>
+__device__ void network_simt_run(const Dims& d, const float* Wt, float* A, float* B1, float* U0) {
+  const int C = d.C, F = d.F;
+  const float* W0T = Wt;
+  const float* b0 = W0T + F * C;
+  const float* cur = b0 + C;
+  gemm_dispatch<MT>(GM_STORE, U0, F, W0T, b0, C, A, 0);
+  __syncthreads();
+  for (int r = 0; r < d.R; r++) {
+    const float* W1T = cur;
+    const float* b1 = W1T + C * C;
+    const float* W2T = b1 + C;
+    const float* b2 = W2T + C * C;
+    cur = b2 + C;
+    for (int e = threadIdx.x; e < C * MT; e += blockDim.x) B1[e] = elu_f(A[e]);
+    __syncthreads();
+    gemm_dispatch<MT>(GM_ELU, B1, C, W1T, b1, C, U0, 0);
+    __syncthreads();
+    gemm_dispatch<MT>(GM_RESID, U0, C, W2T, b2, C, A, 0);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < C * MT; e += blockDim.x) B1[e] = elu_f(A[e]);
+  __syncthreads();
+  const float* WHT = cur;
+  const float* bH = WHT + C * d.NOp;
+  gemm_dispatch<MT>(GM_HEAD, B1, C, WHT, bH, d.NOp, U0, d.ldP);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------
+// Discretized logistic mixture and the frequency table of one channel.
+// Network outputs of a pixel: [0,K) logits, [K,4K) locations mu_{c,k},
+// [4K,7K) log-scales (clamped below at -7), [7K,10K) raw coupling
+// coefficients (tanh).  Coupled locations: m_R = mu_R,
+// m_G = mu_G + alpha x_R, m_B = mu_B + beta x_R + gamma x_G.
+// Boundary b (1..255) sits at e_b = (2b-256)/255; the table is
+//   F(b) = sum_k w_k sigmoid((e_b - m_k)/s_k),
+//   q_b = clamp(rint(65280 F(b)), 0, 65280), Q_b = max(Q_{b-1}, q_b),
+//   cum_b = Q_b + b, cum_256 = 2^16,
+// so every frequency is >= 1 and they sum to 2^16.  Component weights:
+// R: pi_k; G: prop. to pi_k P_Rk(r); B: prop. to pi_k P_Rk(r) P_Gk(g).
+// ---------------------------------------------------------------------
+__device__ __forceinline__ float edge_f(int b) { return __fdiv_rn((float)(2 * b - 256), 255.f); }
+__device__ __forceinline__ float softplus_f(float x) {
+  return x > 0.f ? __fadd_rn(x, log1pf(expf(-x))) : log1pf(expf(x));
+}
+__device__ __forceinline__ float log1mexp_f(float d) {
+  return d <= 0.6931471805599453f ? logf(-expm1f(-d)) : log1pf(-expf(-d));
+}
+
+// log P(v) of one logistic component, stable in both tails:
+// log P = -softplus(-a) - softplus(b) + log(1 - e^{-(a-b)}).
+__device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
+  float inv = expf(-ls);
+  if (v <= 0) return -softplus_f(-__fmul_rn(__fsub_rn(edge_f(1), m), inv));
+  if (v >= 255) return -softplus_f(__fmul_rn(__fsub_rn(edge_f(255), m), inv));
+  float a = __fmul_rn(__fsub_rn(edge_f(v + 1), m), inv);
+  float b = __fmul_rn(__fsub_rn(edge_f(v), m), inv);
+  float d = __fmul_rn(__fdiv_rn(2.f, 255.f), inv);
+  return __fadd_rn(__fsub_rn(-softplus_f(-a), softplus_f(b)), log1mexp_f(d));
+}
+
+// Per-warp scratch of the CDF stage.
+struct WarpScratch {
+  float al[kMaxK], be[kMaxK], w[kMaxK];
+  uint32_t cum[260];
+};
+
+// Per-pixel mixture state held by lane k (< K) for component k.
+struct CompState {
+  float logpi, lw;      // log pi_k, running log weight
+  float mu[3], ls[3], co[3];
+};
+
+__device__ __forceinline__ void comp_init(const float* P, int K, int lane, CompState& cs) {
+  const unsigned full = 0xffffffffu;
+  float logit = lane < K ? P[lane] : -INFINITY;
+  float mx = logit;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+  float e = lane < K ? expf(__fsub_rn(logit, mx)) : 0.f;
+  float s = e;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(full, s, o));
+  // the xor-butterfly sum is the same expression tree in every lane
+  float lse = __fadd_rn(mx, logf(s));
+  cs.logpi = __fsub_rn(logit, lse);
+  cs.lw = cs.logpi;
+  if (lane < K) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      cs.mu[c] = P[K + c * K + lane];
+      cs.ls[c] = fmaxf(P[4 * K + c * K + lane], -7.f);
+      cs.co[c] = tanhf(P[7 * K + c * K + lane]);
+    }
+  }
+}
+
+// Location of channel ch of component (lane) given decoded r, g.
+__device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, int g) {
+  float xr = __fdiv_rn((float)(2 * r - 255), 255.f);
+  float xg = __fdiv_rn((float)(2 * g - 255), 255.f);
+  if (ch == 0) return cs.mu[0];
+  if (ch == 1) return __fadd_rn(cs.mu[1], __fmul_rn(cs.co[0], xr));
+  return __fadd_rn(__fadd_rn(cs.mu[2], __fmul_rn(cs.co[1], xr)), __fmul_rn(cs.co[2], xg));
+}
+
+// Builds cum[0..256] of channel ch in ws.cum (whole warp).  Returns the
+// location of the lane's component (for the posterior update).
+__device__ __forceinline__ float channel_table(const CompState& cs, int K, int ch, int r, int g,
+                                               int lane, WarpScratch& ws) {
+  const unsigned full = 0xffffffffu;
+  float m = 0.f;
+  // component weights: softmax of the running log weights
+  float lw = lane < K ? cs.lw : -INFINITY;
+  float mx = lw;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
+  float e = lane < K ? expf(__fsub_rn(lw, mx)) : 0.f;
+  float s = e;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(full, s, o));
+  if (lane < K) {
+    m = comp_mean(cs, ch, r, g);
+    // y = -(e_b - m)/s * log2(e) = be - b * al
+    float c = __fmul_rn(expf(-cs.ls[ch]), 1.4426950408889634f);
+    ws.al[lane] = __fmul_rn(c, __fdiv_rn(2.f, 255.f));
+    ws.be[lane] = __fmul_rn(c, __fadd_rn(m, __fdiv_rn(256.f, 255.f)));
+    ws.w[lane] = __fdiv_rn(e, s);
+  }
+  __syncwarp();
+  float F[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) F[q] = 0.f;
+  const int b0 = lane * 8;
+  for (int k = 0; k < K; k++) {
+    const float al = ws.al[k], be = ws.be[k], wk = ws.w[k];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      float y = __fmaf_rn(-(float)(b0 + q), al, be);
+      float sg = rcp_approx(__fadd_rn(1.f, ex2_approx(y)));
+      F[q] = __fmaf_rn(wk, sg, F[q]);
+    }
+  }
+  // quantise and running max
+  int Q = 0;
+  int qv[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    int b = b0 + q;
+    int v = __float2int_rn(__fmul_rn(65280.f, F[q]));
+    v = v < 0 ? 0 : (v > kMq ? kMq : v);
+    if (b == 0) v = 0;
+    Q = v > Q ? v : Q;
+    qv[q] = Q;
+  }
+  int pre = Q;  // inclusive max over lanes <= lane
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(full, pre, o);
+    if (lane >= o) pre = t > pre ? t : pre;
+  }
+  int excl = __shfl_up_sync(full, pre, 1);
+  if (lane == 0) excl = 0;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    int v = qv[q] > excl ? qv[q] : excl;
+    ws.cum[b0 + q] = (uint32_t)(v + b0 + q);
+  }
+  if (lane == 0) ws.cum[256] = 65536u;
+  __syncwarp();
+  return m;
+}
+
+// Symbol s with cum_s <= slot < cum_{s+1} (cum strictly increasing).
+__device__ __forceinline__ int table_search(const WarpScratch& ws, uint32_t slot, int lane) {
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    int b = lane * 8 + q;
+    cnt += (b >= 1 && ws.cum[b] <= slot) ? 1 : 0;
+  }
+  return __reduce_add_sync(0xffffffffu, cnt);
+}
+
+// Posterior update after channel ch took value v (lanes < K).
+__device__ __forceinline__ void comp_observe(CompState& cs, int K, int ch, float m, int v, int lane) {
+  if (lane < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, cs.ls[ch], v));
+}
+
+}  // namespace nlc

@@ -1,0 +1,401 @@
+// BF16 local network on the 5th-generation tensor cores (tcgen05 + TMEM).
+//
+// A tile is M = 128 pixels.  Each layer is one chain of
+// tcgen05.mma.cta_group::1.kind::f16 instructions (K = 16 per instruction,
+// FP32 accumulation in TMEM) issued by one thread; the accumulator is read
+// back with tcgen05.ld by all 8 warps (warp w reads TMEM lanes 32(w%4)..+31
+// and half w/4 of the columns), bias/ELU/residual are applied in registers
+// and the next layer's A operand is written to shared memory as BF16 in the
+// canonical no-swizzle K-major layout:
+//   element (r, k) of an R x Kd matrix at
+//   ((r/8) * (Kd/8) + k/8) * 64 + (r%8) * 8 + (k%8)   (BF16 elements)
+// i.e. 8x8 core matrices of 128 contiguous bytes; the leading-dimension byte
+// offset (next core matrix along K) is 128 and the stride-dimension byte
+// offset (next 8-row group) is Kd/8 * 128.
+//
+// Network input: the integer 2v-255 (exact in BF16); the 1/255 of the scaled
+// pixel value (2v-255)/255 is folded into the first-layer weights.  The
+// residual stream stays in FP32 registers; only layer inputs are BF16.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "nlc_common.cuh"
+#include "nlc_model.cuh"
+
+namespace nlc {
+
+constexpr int kTcM = 128;
+constexpr int kTileMax = 128;
+constexpr int kTmemCols = 128;
+constexpr unsigned kMbarSpin = 1u << 22;
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+struct TcPlan {
+  int w0, w1[kMaxR], w2[kMaxR], wh, bias, hbuf, p, mbar, tslot, end;
+};
+
+__host__ __device__ inline TcPlan tc_plan(const Dims& d) {
+  TcPlan p;
+  int o = 0;
+  p.w0 = o;
+  o += d.C * d.Fp * 2;
+  for (int r = 0; r < kMaxR; r++) {
+    p.w1[r] = o;
+    if (r < d.R) o += d.C * d.C * 2;
+    p.w2[r] = o;
+    if (r < d.R) o += d.C * d.C * 2;
+  }
+  p.wh = o;
+  o += d.NOp * d.C * 2;
+  p.bias = o;
+  o += (d.C + 2 * d.R * d.C + d.NOp) * 4;
+  o = align_up(o, 128);
+  p.hbuf = o;
+  o += kTcM * d.C * 2;
+  o = align_up(o, 128);
+  p.p = o;  // P[m][ldP] FP32, aliased with the BF16 context tile X
+  int pbytes = kTcM * d.ldP * 4, xbytes = kTcM * d.Fp * 2;
+  o += pbytes > xbytes ? pbytes : xbytes;
+  o = align_up(o, 16);
+  p.mbar = o;
+  o += 8;
+  p.tslot = o;
+  o += 8;
+  p.end = align_up(o, 128);
+  return p;
+}
+
+__host__ __device__ inline size_t tc_smem_bytes(const Dims& d) { return (size_t)tc_plan(d).end; }
+__host__ __device__ inline size_t umma_halves(const Dims& d) {
+  return (size_t)d.C * d.Fp + 2 * (size_t)d.R * d.C * d.C + (size_t)d.NOp * d.C;
+}
+__host__ __device__ inline size_t bias_floats(const Dims& d) { return (size_t)d.C + 2 * (size_t)d.R * d.C + d.NOp; }
+
+struct TcSmem {
+  unsigned char* base;
+  uint16_t* X;
+  uint16_t* H;
+  float* P;
+  float* bias;
+  uint64_t* mbar;
+  uint32_t* tslot;
+  uint32_t tmem;
+  uint32_t phase;
+  int ok;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__host__ __device__ __forceinline__ int umma_off(int r, int k, int Kd) {
+  return ((r >> 3) * (Kd >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ TcSmem tc_carve(const Dims& d, unsigned char* smem) {
+  TcPlan p = tc_plan(d);
+  TcSmem t;
+  t.base = smem;
+  t.X = reinterpret_cast<uint16_t*>(smem + p.p);
+  t.H = reinterpret_cast<uint16_t*>(smem + p.hbuf);
+  t.P = reinterpret_cast<float*>(smem + p.p);
+  t.bias = reinterpret_cast<float*>(smem + p.bias);
+  t.mbar = reinterpret_cast<uint64_t*>(smem + p.mbar);
+  t.tslot = reinterpret_cast<uint32_t*>(smem + p.tslot);
+  t.tmem = 0;
+  t.phase = 0;
+  t.ok = 1;
+  return t;
+}
+
+// --- PTX wrappers --------------------------------------------------------
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, relative LBO, no swizzle
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(mbar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
+  for (unsigned it = 0; it < kMbarSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+  v[4] = __uint_as_float(r4);
+  v[5] = __uint_as_float(r5);
+  v[6] = __uint_as_float(r6);
+  v[7] = __uint_as_float(r7);
+}
+
+// --- setup / teardown -------------------------------------------------------
+__device__ __forceinline__ void tc_setup(TcSmem& t) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(t.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(t.tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  t.tmem = *t.tslot;
+  t.phase = 0;
+  t.ok = 1;
+}
+
+__device__ __forceinline__ void tc_teardown(TcSmem& t) {
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_load_weights(const Dims& d, const WeightView& w, TcSmem& t) {
+  const int nh = w.umma_halves;  // multiple of 64 (core matrices)
+  const uint4* src = reinterpret_cast<const uint4*>(w.umma);
+  uint4* dst = reinterpret_cast<uint4*>(t.base);
+  for (int i = threadIdx.x; i < nh / 8; i += blockDim.x) dst[i] = src[i];
+  const int nb = (int)bias_floats(d);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) t.bias[i] = w.bias[i];
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
+}
+
+// --- gather ------------------------------------------------------------------
+// X(m, k) = 2v - 255 for feature k = 3p + c of tap p, 0 outside the unit,
+// for k >= F and for empty slots.  Each thread writes 16-byte chunks.
+template <bool kCoherent>
+__device__ __noinline__ void tc_gather(const Unit* units, const PixSlot* slots, const Dims& d, TcSmem& t) {
+  const int Fp = d.Fp, F = d.F, h = d.h, w2 = 2 * h + 1;
+  const int nchunk = kTcM * (Fp / 8);
+  for (int it = threadIdx.x; it < nchunk; it += blockDim.x) {
+    const int m = it % kTcM, kb = it / kTcM;
+    const PixSlot s = slots[m];
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) v[e] = 0.f;
+    if (s.unit >= 0) {
+      const Unit u = units[s.unit];
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        const int k = kb * 8 + e;
+        if (k < F) {
+          const int p = k / 3, c = k - 3 * p;
+          const int ii = s.i + p / w2 - h, jj = s.j + p % w2 - h;
+          if (ii >= 0 && ii < u.Hu && jj >= 0 && jj < u.Wu) {
+            const uint8_t* px =
+                u.img + ((long long)(u.y0 + ii) * u.img_W + (u.x0 + jj)) * 3 + c;
+            const int b = kCoherent ? (int)ld_cg_u8(px) : (int)*px;
+            v[e] = (float)(2 * b - 255);
+          }
+        }
+      }
+    }
+    uint4 q;
+    q.x = pack_bf16(v[0], v[1]);
+    q.y = pack_bf16(v[2], v[3]);
+    q.z = pack_bf16(v[4], v[5]);
+    q.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(t.X + umma_off(m, kb * 8, Fp)) = q;
+  }
+}
+
+// --- network -----------------------------------------------------------------
+__device__ __forceinline__ void tc_issue(const TcSmem& t, uint32_t a_off, uint32_t b_off, int Kd,
+                                         int N) {
+  if (threadIdx.x == 0) {
+    fence_after_sync();
+    const uint32_t a0 = smem_u32(t.base + a_off), b0 = smem_u32(t.base + b_off);
+    const uint32_t sbo = (uint32_t)(Kd / 8) * 128u;
+    const uint32_t idesc = idesc_bf16(kTcM, N);
+    for (int s = 0; s < Kd / 16; s++) {
+      mma_bf16(t.tmem, umma_desc(a0 + 256u * s, 128u, sbo), umma_desc(b0 + 256u * s, 128u, sbo),
+               idesc, s > 0 ? 1u : 0u);
+    }
+    mma_commit(t.mbar);
+  }
+}
+
+__device__ __forceinline__ bool tc_wait(TcSmem& t) {
+  bool ok = mbar_wait(t.mbar, t.phase);
+  t.phase ^= 1u;
+  fence_after_sync();
+  return ok;
+}
+
+__device__ __forceinline__ float elu_tc(float x) { return x > 0.f ? x : expm1f(x); }
+
+// Writes 8 values (columns k0..k0+7) of row r into the BF16 H tile.
+__device__ __forceinline__ void store_h8(uint16_t* H, int r, int k0, int C, const float (&v)[8]) {
+  uint4 q;
+  q.x = pack_bf16(v[0], v[1]);
+  q.y = pack_bf16(v[2], v[3]);
+  q.z = pack_bf16(v[4], v[5]);
+  q.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(H + umma_off(r, k0, C)) = q;
+}
+
+// Runs the whole network on the tile in X; P[m][ldP] = head outputs.
+static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t) {
+  const TcPlan pl = tc_plan(d);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * (warp & 3) + lane;
+  const int half = warp >> 2;
+  const uint32_t tl = t.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const int C = d.C, ch = C / 2, c0 = half * ch;
+  const float* b0 = t.bias;
+  float a[kMaxC / 2];
+  bool ok = true;
+
+  // layer 0: a = X W0^T + b0, H = ELU(a)
+  fence_async_smem();
+  __syncthreads();
+  tc_issue(t, (uint32_t)pl.p, (uint32_t)pl.w0, d.Fp, C);
+  ok &= tc_wait(t);
+#pragma unroll
+  for (int g = 0; g < kMaxC / 16; g++) {
+    if (g < ch / 8) {
+      float v[8];
+      tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        a[8 * g + e] = __fadd_rn(v[e], b0[c0 + 8 * g + e]);
+        v[e] = elu_tc(a[8 * g + e]);
+      }
+      store_h8(t.H, row, c0 + 8 * g, C, v);
+    }
+  }
+  fence_before_sync();
+  fence_async_smem();
+  __syncthreads();
+
+  for (int r = 0; r < d.R; r++) {
+    const float* b1 = t.bias + C + 2 * r * C;
+    const float* b2 = b1 + C;
+    // hidden = ELU(H W1^T + b1)
+    tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w1[r], C, C);
+    ok &= tc_wait(t);
+#pragma unroll
+    for (int g = 0; g < kMaxC / 16; g++) {
+      if (g < ch / 8) {
+        float v[8];
+        tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
+#pragma unroll
+        for (int e = 0; e < 8; e++) v[e] = elu_tc(__fadd_rn(v[e], b1[c0 + 8 * g + e]));
+        store_h8(t.H, row, c0 + 8 * g, C, v);
+      }
+    }
+    fence_before_sync();
+    fence_async_smem();
+    __syncthreads();
+    // a += H W2^T + b2, H = ELU(a)
+    tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w2[r], C, C);
+    ok &= tc_wait(t);
+#pragma unroll
+    for (int g = 0; g < kMaxC / 16; g++) {
+      if (g < ch / 8) {
+        float v[8];
+        tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          a[8 * g + e] = __fadd_rn(a[8 * g + e], __fadd_rn(v[e], b2[c0 + 8 * g + e]));
+          v[e] = elu_tc(a[8 * g + e]);
+        }
+        store_h8(t.H, row, c0 + 8 * g, C, v);
+      }
+    }
+    fence_before_sync();
+    fence_async_smem();
+    __syncthreads();
+  }
+
+  // head: P = H WH^T + bH
+  const float* bh = t.bias + C + 2 * d.R * C;
+  tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.wh, C, d.NOp);
+  ok &= tc_wait(t);
+  const int nh = d.NOp / 2, n0 = half * nh;
+  for (int g = 0; g < nh / 8; g++) {
+    float v[8];
+    tmem_ld8(tl + (uint32_t)(n0 + 8 * g), v);
+    float* o = t.P + (size_t)row * d.ldP + n0 + 8 * g;
+#pragma unroll
+    for (int e = 0; e < 8; e++) o[e] = __fadd_rn(v[e], bh[n0 + 8 * g + e]);
+  }
+  fence_before_sync();
+  __syncthreads();
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+cudaError_t launch_repack_umma(const Dims& d, const float* w, uint16_t* umma, float* bias,
+                               cudaStream_t s);
+
+}  // namespace nlc

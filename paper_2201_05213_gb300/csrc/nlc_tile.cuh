@@ -1,0 +1,251 @@
+// Device helpers shared by the codec kernels: unit lookup, block scans, the
+// warp-level rANS decoder, the per-stream rANS encoder and the tile pipeline
+// (gather -> local network) in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nlc_common.cuh"
+#include "nlc_kernels.cuh"
+#include "nlc_model.cuh"
+#include "nlc_tc.cuh"
+
+namespace nlc {
+
+constexpr int kMT = 64;  // pixels per tile of the FP32 pipeline
+
+// ---------------------------------------------------------------------
+// Shared helpers
+// ---------------------------------------------------------------------
+__device__ __forceinline__ int find_unit_px(const Unit* units, int n, long long q) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (units[mid].px_base <= q) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int find_unit_stream(const Unit* units, int n, int s) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (units[mid].stream_base <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block-wide exclusive scan of one int per thread; returns the exclusive
+// prefix, writes the total to *total (all threads).
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long y = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    if (lane < nw) sh[lane] = y;
+  }
+  __syncthreads();
+  long long excl = x - v + (warp > 0 ? sh[warp - 1] : 0);
+  *total = sh[nw - 1];
+  __syncthreads();
+  return excl;
+}
+
+// Fronts of all units at global step t: pre[u] = exclusive prefix of the
+// front sizes, pre[n_units] = total.  Requires n_units + 1 ints of smem.
+__device__ __forceinline__ int front_scan(const Unit* __restrict__ units, int n_units, int t,
+                                          int h, int sched,
+                          int* pre, long long* sh) {
+  const int per = (n_units + blockDim.x - 1) / blockDim.x;
+  const int u0 = threadIdx.x * per, u1 = min(u0 + per, n_units);
+  long long sum = 0;
+  for (int u = u0; u < u1; u++) {
+    int c = unit_front(units[u], t, h, sched).n;
+    pre[u] = c;
+    sum += c;
+  }
+  long long total;
+  long long run = block_excl_scan(sum, sh, &total);
+  for (int u = u0; u < u1; u++) {
+    int c = pre[u];
+    pre[u] = (int)run;
+    run += c;
+  }
+  if (threadIdx.x == 0) pre[n_units] = (int)total;
+  __syncthreads();
+  return (int)total;
+}
+
+// ---------------------------------------------------------------------
+// rANS: warp-level decoder of one stream position and the per-stream
+// encoder (byte-wise renormalisation, state in [2^23, 2^31)).
+// ---------------------------------------------------------------------
+struct WarpRansDec {
+  uint32_t x;
+  unsigned long long pos, end;
+  uint32_t byte;
+  int used;
+  bool bad;
+
+  __device__ __forceinline__ void prefetch(const uint8_t* base, int lane) {
+    byte = 0;
+    unsigned long long p = pos + (unsigned long long)lane;
+    if (lane < 8 && p < end) byte = base[p];
+    used = 0;
+  }
+  // slot = x mod 2^16, symbol s with cum_s <= slot < cum_{s+1},
+  // x = freq (x >> 16) + slot - cum_s, then shift bytes in while x < 2^23.
+  __device__ __forceinline__ int decode(const WarpScratch& ws, int lane) {
+    const uint32_t slot = x & 0xFFFFu;
+    const int s = table_search(ws, slot, lane);
+    const uint32_t c0 = ws.cum[s], c1 = ws.cum[s + 1];
+    x = (c1 - c0) * (x >> 16) + slot - c0;
+    for (int it = 0; it < 3 && x < kRansL; it++) {
+      uint32_t bt = __shfl_sync(0xffffffffu, byte, used & 7);
+      if (used >= 8 || pos + (unsigned long long)used >= end) bad = true;
+      x = (x << 8) | bt;
+      used++;
+    }
+    if (x < kRansL) bad = true;
+    return s;
+  }
+};
+
+// Encodes symbols k = nsym-1 .. 0 (packed start | freq << 16) ending at
+// slot_end; returns the stream length.  Layout: 4-byte big-endian final
+// state, then the emitted bytes in reverse emission order.
+template <class Get>
+__device__ __forceinline__ int rans_encode_stream(Get get, long long nsym, uint8_t* slot_end) {
+  uint8_t* w = slot_end;
+  uint32_t x = kRansL;
+  for (long long k = nsym - 1; k >= 0; k--) {
+    const uint32_t e = get(k);
+    const uint32_t start = e & 0xFFFFu, f = e >> 16;
+    const uint32_t xmax = ((kRansL >> 16) << 8) * f;
+    while (x >= xmax) {
+      *--w = (uint8_t)(x & 0xFFu);
+      x >>= 8;
+    }
+    x = ((x / f) << 16) + (x % f) + start;
+  }
+  *--w = (uint8_t)x;
+  *--w = (uint8_t)(x >> 8);
+  *--w = (uint8_t)(x >> 16);
+  *--w = (uint8_t)(x >> 24);
+  return (int)(slot_end - w);
+}
+
+// ---------------------------------------------------------------------
+// Tile pipeline (FP32 SIMT network) shared by encode, decode and forward.
+// ---------------------------------------------------------------------
+struct TileSmem {
+  float* Wt;
+  float* A;
+  float* B1;
+  float* U0;
+  WarpScratch* ws;
+  PixSlot* slots;
+  int* pre;
+  long long* sh;
+  int* flag;
+  TcSmem tc;
+};
+
+__host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre) {
+  size_t bytes;
+  if (d.prec == PREC_BF16) {
+    bytes = tc_smem_bytes(d);
+  } else {
+    SimtPlan pl = simt_plan(d, (int)simt_floats(d), kMT);
+    bytes = (size_t)pl.end * 4;
+  }
+  bytes = (bytes + 15) & ~(size_t)15;
+  bytes += sizeof(WarpScratch) * kWarps;
+  bytes += sizeof(PixSlot) * kTileMax;
+  bytes += sizeof(long long) * 33;
+  bytes += sizeof(int) * (n_pre + 1 + 4);
+  return (bytes + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, int n_pre) {
+  TileSmem t;
+  size_t off;
+  if (d.prec == PREC_BF16) {
+    t.tc = tc_carve(d, smem);
+    off = tc_smem_bytes(d);
+    t.Wt = t.A = t.B1 = nullptr;
+    t.U0 = t.tc.P;
+  } else {
+    SimtPlan pl = simt_plan(d, (int)simt_floats(d), kMT);
+    float* f = reinterpret_cast<float*>(smem);
+    t.Wt = f + pl.w_off;
+    t.A = f + pl.a_off;
+    t.B1 = f + pl.b1_off;
+    t.U0 = f + pl.u0_off;
+    off = (size_t)pl.end * 4;
+  }
+  off = (off + 15) & ~(size_t)15;
+  t.ws = reinterpret_cast<WarpScratch*>(smem + off);
+  off += sizeof(WarpScratch) * kWarps;
+  t.slots = reinterpret_cast<PixSlot*>(smem + off);
+  off += sizeof(PixSlot) * kTileMax;
+  t.sh = reinterpret_cast<long long*>(smem + off);
+  off += sizeof(long long) * 33;
+  t.pre = reinterpret_cast<int*>(smem + off);
+  t.flag = t.pre + n_pre + 1;
+  (void)n_pre;
+  return t;
+}
+
+template <int PREC>
+__device__ __forceinline__ constexpr int tile_size() { return PREC == PREC_BF16 ? kTcM : kMT; }
+
+template <int PREC>
+__device__ __forceinline__ void load_weights(const DeviceModel& m, TileSmem& t) {
+  if constexpr (PREC == PREC_BF16) {
+    tc_load_weights(m.d, m.w, t.tc);
+  } else {
+    const int n = m.w.simt_floats;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t.Wt[i] = m.w.simt[i];
+  }
+}
+
+// gather + network for the slots of the tile; P[m][NOp] lands in t.U0.
+template <int PREC, bool kCoherent>
+__device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* units, TileSmem& t) {
+  if constexpr (PREC == PREC_BF16) {
+    tc_gather<kCoherent>(units, t.slots, m.d, t.tc);
+    __syncthreads();
+    tc_network(m.d, t.tc);
+  } else {
+    gather_f32<kMT, kCoherent>(units, t.slots, m.d.h, t.U0);
+    __syncthreads();
+    network_simt_run<kMT>(m.d, t.Wt, t.A, t.B1, t.U0);
+  }
+}
+
+
+__device__ __forceinline__ int unit_streams(const Unit& U, int layout) {
+  return layout == 1 ? U.Hu : 1;
+}
+
+inline int grid_for(long long work, int per, int cap) {
+  long long g = (work + per - 1) / per;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace nlc

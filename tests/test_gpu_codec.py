@@ -1,0 +1,179 @@
+"""End-to-end parity of the CUDA codec through the C ABI.
+
+Decoded pixels must equal the input bit for bit under every schedule
+(Section 4: sequential, wavefront and patch decoding give the same result),
+code lengths must match the oracle's model (|delta bpd| <= 0.01 FP32,
+<= 0.03 BF16) and the bytes must be within 32 bits per stream of the
+tables' ideal length; malformed inputs must be reported, not decoded
+silently.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2201_05213_gb300 import codec as CD
+from paper_2201_05213_gb300 import nlc as N
+
+from gpu_util import DEV, ensure_built, images, make_codec, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SCHEDS = [N.NLC_SCHED_WAVEFRONT, N.NLC_SCHED_RASTER, N.NLC_SCHED_SEQUENTIAL]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _round_trip(codec, imgs, patch, layout, scheds=SCHEDS):
+    dimgs = [to_dev(i) for i in imgs]
+    data, offs = codec.compress(dimgs, patch, layout)
+    sizes = [i.shape[:2] for i in imgs]
+    for sch in scheds:
+        if layout == N.NLC_LAYOUT_UNIT and sch == N.NLC_SCHED_WAVEFRONT:
+            continue
+        outs = codec.decompress(data, offs, sizes, patch, layout, sch)
+        for a, b in zip(outs, imgs):
+            assert np.array_equal(a.cpu().numpy(), b), (patch, layout, sch)
+    return data, offs
+
+
+@pytest.mark.parametrize("prec,cfg", [(N.NLC_FP32, (3, 32, 2, 10)), (N.NLC_BF16, (3, 64, 2, 10)),
+                                      (N.NLC_FP32, (1, 16, 1, 4)), (N.NLC_BF16, (2, 32, 1, 10))])
+@pytest.mark.parametrize("patch,layout", [(0, 1), (16, 1), (0, 0), (13, 0)])
+def test_round_trip_all_schedules(prec, cfg, patch, layout):
+    codec, _ = make_codec(cfg, prec, seed=5, scale=2.0)
+    imgs = images(11, [(33, 41), (16, 16), (1, 7), (9, 1), (2, 2), (20, 3)])
+    _round_trip(codec, imgs, patch, layout)
+
+
+def test_edge_cases():
+    codec, _ = make_codec((3, 32, 2, 10), N.NLC_FP32, seed=6)
+    # empty batch
+    data, offs = codec.compress([], 0, 1) if False else (None, None)
+    out = torch.zeros(16, dtype=torch.uint8, device=DEV)
+    offs = torch.zeros(1, dtype=torch.int64, device=DEV)
+    N.nlc_compress(codec.ctx, [], 0, 1, out, offs)
+    assert N.nlc_sync_status(codec.ctx) == N.NLC_OK
+    assert int(offs[0]) == 0
+    N.nlc_decompress(codec.ctx, out, offs, [], 0, 1, N.NLC_SCHED_WAVEFRONT)
+    # zero-sized images next to real ones; h >= W; single pixel
+    imgs = [np.zeros((0, 5, 3), np.uint8)] + images(12, [(1, 1), (5, 2), (3, 3)])
+    dimgs = [to_dev(i) for i in imgs]
+    data, offs = codec.compress(dimgs, 0, 1)
+    outs = codec.decompress(data, offs, [i.shape[:2] for i in imgs], 0, 1)
+    for a, b in zip(outs, imgs):
+        assert np.array_equal(a.cpu().numpy(), b)
+
+
+@pytest.mark.parametrize("prec", [N.NLC_FP32, N.NLC_BF16])
+@pytest.mark.parametrize("tuning", [(1, 0), (8, 0), (4096, 0), (8, 1), (1, 3)])
+def test_decoder_work_split(prec, tuning):
+    # many pixels per CTA (several tiles per step), one CTA, odd grids
+    cfg = (3, 32, 2, 10)
+    codec, _ = make_codec(cfg, prec, seed=7, scale=2.0)
+    N.nlc_set_tuning(codec.ctx, *tuning)
+    imgs = images(13, [(70, 300), (31, 17), (64, 64)])
+    _round_trip(codec, imgs, 0, 1, [N.NLC_SCHED_WAVEFRONT])
+
+
+def test_deterministic_and_batch_independent():
+    # O12: the encoder's tables of a pixel do not depend on its tile position
+    codec, _ = make_codec((3, 64, 2, 10), N.NLC_BF16, seed=8, scale=2.0)
+    imgs = images(14, [(30, 50), (17, 9), (40, 40)])
+    d1, o1 = codec.compress([to_dev(i) for i in imgs], 0, 1)
+    d2, o2 = codec.compress([to_dev(i) for i in imgs], 0, 1)
+    assert torch.equal(o1, o2) and torch.equal(d1[: int(o1[-1])], d2[: int(o2[-1])])
+    rev = imgs[::-1]
+    d3, o3 = codec.compress([to_dev(i) for i in rev], 0, 1)
+    a = d1.cpu().numpy()
+    b = d3.cpu().numpy()
+    o1n, o3n = o1.cpu().numpy(), o3.cpu().numpy()
+    for k in range(3):
+        r = 2 - k
+        assert np.array_equal(a[o1n[k]:o1n[k + 1]], b[o3n[r]:o3n[r + 1]])
+
+
+@pytest.mark.parametrize("prec,tol", [(N.NLC_FP32, 0.01), (N.NLC_BF16, 0.03)])
+def test_code_length_matches_oracle(prec, tol):
+    cfg = (3, 32, 2, 10) if prec == N.NLC_FP32 else (3, 64, 2, 10)
+    codec, w = make_codec(cfg, prec, seed=9)
+    imgs = images(15, [(40, 48), (24, 24)])
+    dims = sum(3 * i.shape[0] * i.shape[1] for i in imgs)
+    dimgs = [to_dev(i) for i in imgs]
+    _, bits = codec.forward(dimgs, 0, params=False, bits=True)
+    gpu_bpd = float(bits.double().sum()) / dims
+    ref_bits = 0.0
+    for im in imgs:
+        P = O.forward_image(cfg, w, im).reshape(-1, 10 * cfg[3])
+        pix = im.reshape(-1, 3)
+        ref_bits += sum(O.pixel_bits(cfg[3], P[q], *pix[q]) for q in range(len(pix)))
+    assert abs(gpu_bpd - ref_bits / dims) <= tol, (gpu_bpd, ref_bits / dims)
+    # actual bytes: within 32 bits per stream (+ headers) of the tables' ideal length
+    data, offs = codec.compress(dimgs, 0, 1)
+    P, _ = codec.forward(dimgs, 0)
+    pix = torch.cat([t.reshape(-1, 3) for t in dimgs])
+    cum = codec.tables(P, pix)
+    ideal = CD.ideal_bits_from_tables(cum, pix)
+    nstreams = sum(i.shape[0] for i in imgs)
+    payload = int(offs[-1]) - sum(32 + 4 * i.shape[0] for i in imgs)
+    assert 8 * payload <= ideal + 32 * nstreams + 8 * 16 * len(imgs)
+    assert 8 * payload >= ideal - 1
+
+
+def test_malformed_input_is_reported():
+    codec, w = make_codec((2, 16, 1, 4), N.NLC_FP32, seed=10, scale=2.0)
+    imgs = images(16, [(20, 30), (12, 12)])
+    dimgs = [to_dev(i) for i in imgs]
+    data, offs = codec.compress(dimgs, 0, 1)
+    sizes = [i.shape[:2] for i in imgs]
+    # flipped payload byte: reported or at least not silently equal
+    bad = data.clone()
+    pos = int(offs[0]) + 32 + 4 * 20 + 40
+    bad[pos] ^= 0x5A
+    outs = codec.decompress(bad, offs, sizes, 0, 1, check=False)
+    code = N.nlc_sync_status(codec.ctx)
+    assert code == N.NLC_ERR_CORRUPT or not np.array_equal(outs[0].cpu().numpy(), imgs[0])
+    # broken magic
+    bad = data.clone()
+    bad[int(offs[1])] ^= 0xFF
+    codec.decompress(bad, offs, sizes, 0, 1, check=False)
+    assert N.nlc_sync_status(codec.ctx) == N.NLC_ERR_CORRUPT
+    # truncated container
+    offs2 = offs.clone()
+    offs2[2] = offs2[2] - 40
+    codec.decompress(data, offs2, sizes, 0, 1, check=False)
+    assert N.nlc_sync_status(codec.ctx) == N.NLC_ERR_CORRUPT
+    # wrong sizes for the container
+    codec.decompress(data, offs, [(20, 31), (12, 12)], 0, 1, check=False)
+    assert N.nlc_sync_status(codec.ctx) == N.NLC_ERR_CORRUPT
+    # other weights
+    other, _ = make_codec((2, 16, 1, 4), N.NLC_FP32, seed=11, scale=2.0)
+    other.decompress(data, offs, sizes, 0, 1, check=False)
+    assert N.nlc_sync_status(other.ctx) == N.NLC_ERR_WEIGHTS
+    # output too small
+    out = torch.zeros(64, dtype=torch.uint8, device=DEV)
+    o = torch.zeros(3, dtype=torch.int64, device=DEV)
+    N.nlc_compress(codec.ctx, dimgs, 0, 1, out, o)
+    assert N.nlc_sync_status(codec.ctx) == N.NLC_ERR_CAPACITY
+    # wavefront on one stream per unit is an argument error
+    with pytest.raises(N.NLCError):
+        codec.decompress(data, offs, sizes, 0, 0, N.NLC_SCHED_WAVEFRONT)
+
+
+def test_oracle_decodes_same_partition_same_pixels():
+    # the oracle's own raster codec and the GPU codec agree on the decoded image
+    cfg = (3, 32, 2, 10)
+    codec, w = make_codec(cfg, N.NLC_FP32, seed=0)
+    img = images(0, [(32, 32)])[0]
+    words, lens, bm, bq = O.encode_image(cfg, w, img, 0, 0)
+    dec, ok = O.decode_image(cfg, w, words, lens, 32, 32, 0, 0)
+    assert ok and (dec == img).all()
+    data, offs = codec.compress([to_dev(img)], 0, 0)
+    outs = codec.decompress(data, offs, [(32, 32)], 0, 0, N.NLC_SCHED_SEQUENTIAL)
+    assert np.array_equal(outs[0].cpu().numpy(), dec)
+    # one stream each: the payloads differ only through FP32 vs FP64 tables
+    assert abs((int(offs[1]) - 36) - len(words)) <= 16
+    assert 8 * len(words) <= bq + 32 + 1
