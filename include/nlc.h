@@ -148,6 +148,32 @@ int nlc_compress_bound(const int32_t* h_H, const int32_t* h_W, int n, int patch,
 int nlc_compress(nlc_ctx* ctx, const nlc_image_in* h_imgs, int n, int patch, int layout,
                  uint8_t* d_out, size_t cap, uint64_t* d_offsets, nlc_stream stream);
 
+/* Scratch capacity of nlc_compress_noalloc, in bytes.  A batch needs about
+ * 18 bytes per pixel, 16 per rANS stream and 100 per coding unit and image
+ * (32 MiB holds e.g. one 1024 x 1024 image or forty 256 x 256 images). */
+#define NLC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* nlc_compress without any device allocation.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc at the time they compress,
+ * e.g. a process whose framework allocator has reserved all device memory,
+ * a real-time thread that cannot absorb cudaMalloc's implicit device
+ * synchronisation and unbounded latency, or a deployment whose device memory
+ * budget is fixed when the library is loaded.  Same arguments, output and
+ * asynchrony as nlc_compress (byte-identical containers), but the call's
+ * scratch (batch plan, per-symbol tables, per-stream bytes) is a file-scope
+ * device array of NLC_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until exit; the caller still owns the images, d_out and
+ * d_offsets.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture.  Batches needing more scratch are rejected
+ * with NLC_ERR_CAPACITY before anything is launched.  All calls share the one
+ * array, which keeps the last call's contents (nothing in it needs to start
+ * at zero): calls that overlap on the GPU, from any context or stream, race,
+ * so serialise them.  The context must already exist (nlc_create allocates);
+ * this call itself allocates nothing. */
+int nlc_compress_noalloc(nlc_ctx* ctx, const nlc_image_in* h_imgs, int n, int patch, int layout,
+                         uint8_t* d_out, size_t cap, uint64_t* d_offsets, nlc_stream stream);
+
 /* Decompresses n containers (d_in + d_offsets[i] .. d_offsets[i+1]) into
  * caller-allocated images whose H, W must match the containers.  `patch`
  * and `layout` must be those used to compress; `schedule` is an

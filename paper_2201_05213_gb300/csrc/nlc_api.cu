@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "../../include/nlc.h"
@@ -582,5 +583,77 @@ extern "C" int nlc_train_step(nlc_ctx* x, const uint8_t* d_batch, int N, int H, 
     CUDA_TRY(cudaMemcpyAsync(h_loss, x->d_loss, 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
   }
+  return NLC_OK;
+}
+
+// ---------------------------------------------------------------------
+// Compression without allocation (nlc_compress_noalloc).
+//
+// The batch plan, the per-symbol staging tables and the per-stream byte
+// slots live in one file-scope device array instead of the context's
+// workspace.  Its name is only a host-side stand-in for the device array, so
+// host code asks the runtime for the device address once per device (with
+// that device current) and passes that pointer to the kernels.  No byte of
+// the array needs to start at zero: every call writes each byte it reads
+// before reading it.  All calls share the array, so calls that overlap on
+// the GPU (on different streams, or from different contexts) race.
+// ---------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NLC_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256];
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(NLC_ERR_UNSUPPORTED, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(NLC_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return NLC_OK;
+}
+
+extern "C" int nlc_compress_noalloc(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch,
+                                    int layout, uint8_t* d_out, size_t cap, uint64_t* d_offsets,
+                                    nlc_stream stream) {
+  if (!x || (n > 0 && !imgs) || !d_offsets || (layout != 0 && layout != 1))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  std::vector<int32_t> H(n), W(n);
+  std::vector<const void*> data(n);
+  std::vector<uint8_t*> ptrs(n);
+  for (int i = 0; i < n; i++) {
+    H[i] = imgs[i].H;
+    W[i] = imgs[i].W;
+    data[i] = imgs[i].data;
+    ptrs[i] = const_cast<uint8_t*>(imgs[i].data);
+  }
+  int rc = check_images(n, H.data(), W.data(), data.data(), patch);
+  if (rc) return rc;
+  if (!d_out && cap > 0) return fail(NLC_ERR_ARG, "d_out is NULL");
+  Batch b;
+  rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, layout, NLC_SCHED_RASTER, b);
+  if (rc) return rc;
+  CodecBufs cb;
+  const size_t need = layout_bufs(b, nullptr, cb, x->d_status, true);
+  if (need > (size_t)NLC_NOALLOC_SCRATCH_BYTES)
+    return fail(NLC_ERR_CAPACITY,
+                "batch needs %zu bytes of scratch but nlc_compress_noalloc has %zu; split the "
+                "batch or use nlc_compress",
+                need, (size_t)NLC_NOALLOC_SCRATCH_BYTES);
+  void* base = nullptr;
+  if ((rc = noalloc_scratch(&base))) return rc;
+  layout_bufs(b, static_cast<unsigned char*>(base), cb, x->d_status, true);
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = ensure_packed(x, s))) return rc;
+  if ((rc = upload_batch(b, cb, s))) return rc;
+  CUDA_TRY(launch_encode(model_view(x), cb, layout, patch, d_out, (unsigned long long)cap,
+                         reinterpret_cast<unsigned long long*>(d_offsets), x->sm_count, s));
   return NLC_OK;
 }

@@ -37,6 +37,7 @@ EXPORTS = [
     "nlc_get_weights", "nlc_set_weights", "nlc_weight_hash", "nlc_sync_status", "nlc_set_tuning",
     "nlc_compress_bound", "nlc_compress", "nlc_decompress", "nlc_forward", "nlc_tables",
     "nlc_rans_encode", "nlc_rans_decode", "nlc_train_step", "nlc_loss_grad",
+    "nlc_compress_noalloc",
 ]
 
 
@@ -88,6 +89,7 @@ def load():
             L.nlc_rans_decode.argtypes = [p, p, i64, p, p, p, i, p, p]
             L.nlc_train_step.argtypes = [p, p, i, i, i, f, p, p]
             L.nlc_loss_grad.argtypes = [p, p, i, i, i, p, p, p]
+            L.nlc_compress_noalloc.argtypes = [p, p, i, i, i, p, sz, p, p]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -192,6 +194,17 @@ def nlc_compress(ctx, imgs, patch, layout, out, offsets, stream=None):
     arr = _images(imgs)
     return _check(load().nlc_compress(ctx, arr, len(imgs), patch, layout, _ptr(out),
                                       out.numel(), _ptr(offsets), _stream(stream)))
+
+
+def nlc_compress_noalloc(ctx, imgs, patch, layout, out, offsets, stream=None):
+    """nlc_compress with the library's fixed device scratch instead of its
+    workspace: the call itself allocates no device memory."""
+    arr = _images(imgs)
+    return _check(load().nlc_compress_noalloc(ctx, arr, len(imgs), patch, layout, _ptr(out),
+                                              out.numel(), _ptr(offsets), _stream(stream)))
+
+
+NLC_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def nlc_decompress(ctx, data, offsets, outs, patch, layout, schedule, stream=None):
