@@ -34,14 +34,24 @@ METRIC = "decoded pixels/s and bpd vs same-GPU sequential decode, 32^2-2048^2 RG
 UNIT = "decoded px/s"
 CFG = (3, 64, 2, 10)
 PATCH = 256
-SIZES = [(2048, 2048)] + [(1024, 1024)] * 8
+WORKLOADS = {
+    # the headline configuration (one 2048^2 and eight 1024^2 images)
+    "full": [(2048, 2048)] + [(1024, 1024)] * 8,
+    # one 1024^2 image: the small case for profiler captures
+    "small": [(1024, 1024)],
+}
+SIZES = WORKLOADS["full"]
 SEED = 4
 N_POLY = 64
 L2_BYTES = 129 * 2 ** 20
 
 
 def workload_name():
-    return "1x2048^2 + 8x1024^2 RGB, 256^2 patches, h=3 C=64 R=2 K=10, BF16 net"
+    imgs = {}
+    for s in SIZES:
+        imgs[s] = imgs.get(s, 0) + 1
+    desc = " + ".join(f"{n}x{h}^2" if h == w else f"{n}x{h}x{w}" for (h, w), n in imgs.items())
+    return f"{desc} RGB, 256^2 patches, h=3 C=64 R=2 K=10, BF16 net"
 
 
 def _measured_peaks():
@@ -197,7 +207,10 @@ def main():
     ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--no-seq", action="store_true", help="skip the sequential baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    global SIZES
+    SIZES = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -277,6 +290,19 @@ def main():
         ms = float(t[0])
     value = world * n_px / (ms / 1e3)
 
+    # per-step latency against the dependency-bound step count (untimed run)
+    N.nlc_decode_profile(codec.ctx, 1, read=False)
+    decode()
+    cnt = N.nlc_decode_profile(codec.ctx, 0).astype(np.float64)
+    steps_T = max(int(cnt[7]), 1)
+    ctas = max(int(cnt[6]), 1)
+    mhz = 2070.0
+    phase_us = {name: float(cnt[i]) / ctas / steps_T / mhz
+                for i, name in enumerate(["front", "slots", "gather_network", "coding", "barrier"])}
+    phases = {"steps": steps_T, "ctas": ctas, "tiles_per_cta_step": float(cnt[5]) / ctas / steps_T,
+              "us_per_step_measured": 1000.0 * ms / steps_T,
+              "us_per_step_by_phase_at_2070MHz": phase_us}
+
     # end to end through the C ABI with host buffers
     h_data = data[:total_bytes].cpu().pin_memory()
     h_offs = offs.cpu().pin_memory()
@@ -318,18 +344,20 @@ def main():
             torch.cuda.synchronize()
             s0 = torch.cuda.Event(enable_timing=True)
             s1 = torch.cuda.Event(enable_timing=True)
+            N.nlc_set_tuning(codec.ctx, 1, 0)  # one pixel (image) per CTA and step
             s0.record(stream)
             N.nlc_decompress(codec.ctx, data, offs, outs, PATCH, N.NLC_LAYOUT_ROW,
                              N.NLC_SCHED_SEQUENTIAL, stream)
             s1.record(stream)
             s1.synchronize()
+            N.nlc_set_tuning(codec.ctx, 8, 0)
             codec.check()
             seq_ms = s0.elapsed_time(s1)
             for a, b in zip(outs, imgs):
                 assert np.array_equal(a.cpu().numpy(), b), "sequential round trip differs"
             extra["sequential_baseline"] = {
                 "value": n_px / (seq_ms / 1e3), "unit": UNIT, "ms": seq_ms,
-                "steps": 2048 * 2048, "speedup": seq_ms / ms,
+                "steps": max(h * w_ for h, w_ in SIZES), "speedup": seq_ms / ms,
                 "how": "same library and containers, NLC_SCHED_SEQUENTIAL (one pixel per image "
                        "per step, patches of an image one after another), one full run"}
         oracle_bpd, _ = oracle_sample_bpd(w.astype(np.float64), imgs, n=192)
@@ -373,7 +401,8 @@ def main():
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded generator; model "
             "trained in-run on seeded crops)",
             "config": {"workload": workload_name(), "images": len(SIZES), "pixels": n_px,
-                       "patch": PATCH, "units": 192, "h": CFG[0], "C": CFG[1], "R": CFG[2],
+                       "patch": PATCH, "units": sum(((h + PATCH - 1) // PATCH) * ((w + PATCH - 1) // PATCH)
+                                                    for h, w in SIZES), "h": CFG[0], "C": CFG[1], "R": CFG[2],
                        "K": CFG[3], "schedule": "wavefront", "layout": "row streams",
                        "l2": "flushed before every timed step (256 MiB write)"},
             "roofline": roof,
@@ -382,6 +411,7 @@ def main():
                     "d2h_bytes_per_step": 3 * n_px},
             "gpu_launches": 5 * args.steps,
             "clocks": clk,
+            "decode_phases": phases,
             **extra,
         }
         if not args.no_cpu:

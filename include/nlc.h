@@ -20,6 +20,8 @@
  *     library owns only the context and a device workspace that it grows on
  *     demand (so the first call with a larger batch allocates).
  *   - Images are uint8 H x W x 3 (RGB), C-contiguous, row stride 3 W bytes.
+ *     Container buffers (d_out of the compress calls, d_in of
+ *     nlc_decompress) must be 16-byte aligned (NLC_ERR_ARG otherwise).
  *   - Calls taking a `stream` are asynchronous on that stream (NULL = the
  *     legacy default stream).  Argument errors are detected synchronously and
  *     returned.  Errors found on the device (corrupt stream, weight mismatch,
@@ -127,6 +129,17 @@ int nlc_sync_status(nlc_ctx* ctx, nlc_stream stream);
  * to each CTA (default 8) and uses at most max_ctas CTAs (0 = as many as can
  * be co-resident). */
 int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
+
+/* Decoder phase profile (per-step latency against the dependency-bound step
+ * count of Section 3).  enable != 0 makes the following nlc_decompress calls
+ * record, in thread 0 of every CTA, clock64 cycles spent per phase; a
+ * non-NULL h_counters (8 uint64) receives the totals accumulated since the
+ * last read, summed over CTAs, and clears them:
+ *   [0] front bookkeeping, [1] tile slot assignment, [2] context gather and
+ *   local network, [3] per-pixel CDF + rANS coding, [4] grid barrier,
+ *   [5] tiles processed, [6] CTAs, [7] decode steps (of CTA 0).
+ * Synchronises the device when reading or changing the mode. */
+int nlc_decode_profile(nlc_ctx* ctx, int enable, uint64_t* h_counters);
 
 /* Upper bound of the compressed size of n images with the given sizes, unit
  * partition and layout: per image 32 + 4 n_streams + 6 H W + 4 n_streams

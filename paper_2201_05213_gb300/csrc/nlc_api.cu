@@ -57,6 +57,7 @@ struct nlc_ctx {
   size_t ws_cap = 0;
   int px_per_cta = 8;
   int max_ctas = 0;
+  unsigned long long* d_prof = nullptr;  // decoder phase counters while profiling
 };
 
 extern "C" const char* nlc_last_error(void) { return g_err; }
@@ -122,6 +123,7 @@ extern "C" int nlc_destroy(nlc_ctx* x) {
   cudaFree(x->d_v);
   cudaFree(x->d_grad);
   cudaFree(x->d_loss);
+  cudaFree(x->d_prof);
   cudaFree(x->ws);
   delete x;
   return NLC_OK;
@@ -230,6 +232,29 @@ extern "C" int nlc_sync_status(nlc_ctx* x, nlc_stream stream) {
     case ST_TIMEOUT: return fail(NLC_ERR_TIMEOUT, "a bounded device wait timed out");
     default: return fail(st, "device status %d", st);
   }
+}
+
+extern "C" int nlc_decode_profile(nlc_ctx* x, int enable, uint64_t* h_counters) {
+  if (!x) return fail(NLC_ERR_ARG, "ctx is NULL");
+  if (h_counters) {
+    if (x->d_prof) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      CUDA_TRY(cudaMemcpy(h_counters, x->d_prof, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemset(x->d_prof, 0, 8 * sizeof(uint64_t)));
+    } else {
+      memset(h_counters, 0, 8 * sizeof(uint64_t));
+    }
+  }
+  if (enable && !x->d_prof) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMalloc((void**)&x->d_prof, 8 * sizeof(uint64_t)));
+    CUDA_TRY(cudaMemset(x->d_prof, 0, 8 * sizeof(uint64_t)));
+  } else if (!enable && x->d_prof) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaFree(x->d_prof);
+    x->d_prof = nullptr;
+  }
+  return NLC_OK;
 }
 
 extern "C" int nlc_set_tuning(nlc_ctx* x, int px_per_cta, int max_ctas) {
@@ -429,6 +454,7 @@ extern "C" int nlc_compress(nlc_ctx* x, const nlc_image_in* imgs, int n, int pat
   int rc = check_images(n, H.data(), W.data(), data.data(), patch);
   if (rc) return rc;
   if (!d_out && cap > 0) return fail(NLC_ERR_ARG, "d_out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_out) % 16) return fail(NLC_ERR_ARG, "d_out must be 16-byte aligned");
   Batch b;
   rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, layout, NLC_SCHED_RASTER, b);
   if (rc) return rc;
@@ -450,6 +476,7 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   if (!x || (n > 0 && (!outs || !d_in || !d_offsets)) || (layout != 0 && layout != 1))
     return fail(NLC_ERR_ARG, "bad arguments");
   if (schedule < 0 || schedule > 2) return fail(NLC_ERR_ARG, "unknown schedule %d", schedule);
+  if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(NLC_ERR_ARG, "d_in must be 16-byte aligned");
   if (layout == NLC_LAYOUT_UNIT && schedule == NLC_SCHED_WAVEFRONT)
     return fail(NLC_ERR_ARG, "one stream per unit can only be decoded in raster order");
   std::vector<int32_t> H(n), W(n);
@@ -484,6 +511,7 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   // the barrier's arrival counter reaches grid * T; keep it within 32 bits
   if ((long long)grid * b.T >= (1LL << 32) - 1) grid = 1;
   const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
+  cb.prof = x->d_prof;
   CUDA_TRY(launch_decode(m, cb, d_in, reinterpret_cast<const unsigned long long*>(d_offsets),
                          layout, patch, sched, (int)b.T, grid, s));
   return NLC_OK;
@@ -637,6 +665,7 @@ extern "C" int nlc_compress_noalloc(nlc_ctx* x, const nlc_image_in* imgs, int n,
   int rc = check_images(n, H.data(), W.data(), data.data(), patch);
   if (rc) return rc;
   if (!d_out && cap > 0) return fail(NLC_ERR_ARG, "d_out is NULL");
+  if (reinterpret_cast<uintptr_t>(d_out) % 16) return fail(NLC_ERR_ARG, "d_out must be 16-byte aligned");
   Batch b;
   rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, layout, NLC_SCHED_RASTER, b);
   if (rc) return rc;

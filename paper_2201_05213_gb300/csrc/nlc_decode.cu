@@ -22,6 +22,7 @@ struct DecodeArgs {
   const unsigned long long* st_end;
   unsigned* bar;
   int* status;
+  unsigned long long* prof;  // optional per-phase cycle counters
 };
 
 template <int PREC>
@@ -38,8 +39,14 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
   const int K = d.K, ldP = d.ldP, h = d.h;
   unsigned my_gen = 0;
   const unsigned G = gridDim.x;
+  // phase cycles of thread 0: front scan, slot fill, gather + network,
+  // per-pixel coding, grid barrier
+  const bool prof = a.prof != nullptr && threadIdx.x == 0;
+  long long ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, tiles = 0, tc = 0, tn = 0;
   for (int step = 0; step < a.T; step++) {
+    if (prof) tc = clock64();
     const int F = front_scan(a.units, a.n_units, step, h, a.sched, t.pre, t.sh);
+    if (prof) { tn = clock64(); ph0 += tn - tc; tc = tn; }
     const long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
     for (long long base = lo; base < hi; base += MT) {
       const int n = (int)min((long long)MT, hi - base);
@@ -62,7 +69,9 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
         t.slots[s] = ps;
       }
       __syncthreads();
-      tile_network<PREC, true>(a.m, a.units, t);
+      if (prof) { tn = clock64(); ph1 += tn - tc; tc = tn; tiles++; }
+      tile_network<PREC, true>(a.m, a.units, t, n);
+      if (prof) { tn = clock64(); ph2 += tn - tc; tc = tn; }
       for (int s = warp; s < n; s += kWarps) {
         const PixSlot ps = t.slots[s];
         const Unit U = a.units[ps.unit];
@@ -97,12 +106,24 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
         }
       }
       __syncthreads();
+      if (prof) { tn = clock64(); ph3 += tn - tc; tc = tn; }
     }
     if (G > 1) {
       if (!grid_barrier(a.bar, a.bar + 1, G, my_gen, a.status, t.flag)) break;
     } else {
       __syncthreads();
     }
+    if (prof) ph4 += clock64() - tc;
+  }
+  if (prof) {
+    atomicAdd(a.prof + 0, (unsigned long long)ph0);
+    atomicAdd(a.prof + 1, (unsigned long long)ph1);
+    atomicAdd(a.prof + 2, (unsigned long long)ph2);
+    atomicAdd(a.prof + 3, (unsigned long long)ph3);
+    atomicAdd(a.prof + 4, (unsigned long long)ph4);
+    atomicAdd(a.prof + 5, (unsigned long long)tiles);
+    atomicAdd(a.prof + 6, 1ull);
+    if (blockIdx.x == 0) atomicAdd(a.prof + 7, (unsigned long long)a.T);
   }
   if constexpr (PREC == PREC_BF16) tc_teardown(t.tc);
 }
@@ -147,6 +168,7 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   a.st_end = b.st_end;
   a.bar = b.bar;
   a.status = b.status;
+  a.prof = b.prof;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
   const void* fn = decode_fn(m.d.prec);
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       t.slots[s] = ps;
     }
     __syncthreads();
-    tile_network<PREC, false>(m, units, t);
+    tile_network<PREC, false>(m, units, t, (int)min((long long)MT, n_px - tile * MT));
     for (int s = warp; s < MT; s += kWarps) {
       const PixSlot ps = t.slots[s];
       if (ps.unit < 0) continue;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       t.slots[s] = ps;
     }
     __syncthreads();
-    tile_network<PREC, false>(m, units, t);
+    tile_network<PREC, false>(m, units, t, (int)min((long long)MT, n_px - tile * MT));
     for (int s = warp; s < MT; s += kWarps) {
       const PixSlot ps = t.slots[s];
       if (ps.unit < 0) continue;

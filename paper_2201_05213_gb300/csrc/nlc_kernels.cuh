@@ -47,6 +47,7 @@ struct CodecBufs {
   unsigned long long* st_end;
   unsigned* bar;                 // 2 words: arrivals, generation
   int* status;
+  unsigned long long* prof = nullptr;  // decoder phase cycle counters (8), optional
 };
 
 // Launchers (return cudaError_t of the launch).

@@ -207,31 +207,53 @@ __device__ void network_simt_run(const Dims& d, const float* Wt, float* A, float
 // so every frequency is >= 1 and they sum to 2^16.  Component weights:
 // R: pi_k; G: prop. to pi_k P_Rk(r); B: prop. to pi_k P_Rk(r) P_Gk(g).
 // ---------------------------------------------------------------------
-__device__ __forceinline__ float edge_f(int b) { return __fdiv_rn((float)(2 * b - 256), 255.f); }
-__device__ __forceinline__ float softplus_f(float x) {
-  return x > 0.f ? __fadd_rn(x, log1pf(expf(-x))) : log1pf(expf(x));
+constexpr float kInv255 = 1.f / 255.f;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Boundary e_b = (2b - 256)/255 and the scaled value x_v = (2v - 255)/255.
+__device__ __forceinline__ float edge_f(int b) { return __fmul_rn((float)(2 * b - 256), kInv255); }
+__device__ __forceinline__ float xval_f(int v) { return __fmul_rn((float)(2 * v - 255), kInv255); }
+
+// e^x and log x through the MUFU ex2 / lg2 approximations (deterministic).
+__device__ __forceinline__ float exp_f(float x) { return ex2_approx(__fmul_rn(x, kLog2e)); }
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
+__device__ __forceinline__ float log_f(float x) { return __fmul_rn(lg2_approx(x), 0.6931471805599453f); }
+
+// softplus(x) = max(x, 0) + log(1 + e^{-|x|})
+__device__ __forceinline__ float softplus_f(float x) {
+  return __fadd_rn(fmaxf(x, 0.f), log_f(__fadd_rn(1.f, exp_f(-fabsf(x)))));
+}
+// log(1 - e^{-d}), d > 0 (accurate expm1 for small d, Maechler 2012)
 __device__ __forceinline__ float log1mexp_f(float d) {
-  return d <= 0.6931471805599453f ? logf(-expm1f(-d)) : log1pf(-expf(-d));
+  return d <= 0.6931471805599453f ? log_f(-expm1f(-d)) : log_f(__fsub_rn(1.f, exp_f(-d)));
 }
 
 // log P(v) of one logistic component, stable in both tails:
-// log P = -softplus(-a) - softplus(b) + log(1 - e^{-(a-b)}).
+// log P = -softplus(-a) - softplus(b) + log(1 - e^{-(a-b)}), a - b = (2/255)/s.
 __device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
-  float inv = expf(-ls);
+  const float inv = exp_f(-ls);
   if (v <= 0) return -softplus_f(-__fmul_rn(__fsub_rn(edge_f(1), m), inv));
   if (v >= 255) return -softplus_f(__fmul_rn(__fsub_rn(edge_f(255), m), inv));
-  float a = __fmul_rn(__fsub_rn(edge_f(v + 1), m), inv);
-  float b = __fmul_rn(__fsub_rn(edge_f(v), m), inv);
-  float d = __fmul_rn(__fdiv_rn(2.f, 255.f), inv);
-  return __fadd_rn(__fsub_rn(-softplus_f(-a), softplus_f(b)), log1mexp_f(d));
+  const float a = __fmul_rn(__fsub_rn(edge_f(v + 1), m), inv);
+  const float b = __fmul_rn(__fsub_rn(edge_f(v), m), inv);
+  // d = (2/255) e^{-ls}; for d < e^-14 log(1 - e^{-d}) = log d + O(d) is taken
+  // in the log domain, which stays finite when e^{-ls} underflows
+  const float logd = __fsub_rn(-4.848116f, ls);
+  const float lme = logd < -14.f ? logd : log1mexp_f(__fmul_rn(2.f * kInv255, inv));
+  return __fadd_rn(__fsub_rn(-softplus_f(-a), softplus_f(b)), lme);
 }
 
 // Per-warp scratch of the CDF stage.
-struct WarpScratch {
-  float al[kMaxK], be[kMaxK], w[kMaxK];
+struct alignas(16) WarpScratch {
+  float al[kMaxK], be[kMaxK], w[kMaxK], rr[kMaxK];
   uint32_t cum[260];
 };
+static_assert(sizeof(WarpScratch) % 16 == 0, "WarpScratch keeps 16-byte alignment in arrays");
+
 
 // Per-pixel mixture state held by lane k (< K) for component k.
 struct CompState {
@@ -245,12 +267,12 @@ __device__ __forceinline__ void comp_init(const float* P, int K, int lane, CompS
   float mx = logit;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
-  float e = lane < K ? expf(__fsub_rn(logit, mx)) : 0.f;
+  float e = lane < K ? exp_f(__fsub_rn(logit, mx)) : 0.f;
   float s = e;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(full, s, o));
   // the xor-butterfly sum is the same expression tree in every lane
-  float lse = __fadd_rn(mx, logf(s));
+  float lse = __fadd_rn(mx, log_f(s));
   cs.logpi = __fsub_rn(logit, lse);
   cs.lw = cs.logpi;
   if (lane < K) {
@@ -265,8 +287,7 @@ __device__ __forceinline__ void comp_init(const float* P, int K, int lane, CompS
 
 // Location of channel ch of component (lane) given decoded r, g.
 __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, int g) {
-  float xr = __fdiv_rn((float)(2 * r - 255), 255.f);
-  float xg = __fdiv_rn((float)(2 * g - 255), 255.f);
+  const float xr = xval_f(r), xg = xval_f(g);
   if (ch == 0) return cs.mu[0];
   if (ch == 1) return __fadd_rn(cs.mu[1], __fmul_rn(cs.co[0], xr));
   return __fadd_rn(__fadd_rn(cs.mu[2], __fmul_rn(cs.co[1], xr)), __fmul_rn(cs.co[2], xg));
@@ -274,6 +295,13 @@ __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, i
 
 // Builds cum[0..256] of channel ch in ws.cum (whole warp).  Returns the
 // location of the lane's component (for the posterior update).
+//
+// Lane l owns the boundaries b = 8l..8l+7.  With
+// y_k(b) = -(e_b - m_k)/s_k log2(e) = be_k - b al_k, component k's logistic
+// is 1/(1 + 2^y): one ex2 at the lane's first boundary, then 2^y of the next
+// boundary by one multiply with 2^-al_k, and one rcp per boundary.  The sum
+// runs over k in a fixed order, so F(b) is the same expression of the pixel's
+// parameters in every kernel.
 __device__ __forceinline__ float channel_table(const CompState& cs, int K, int ch, int r, int g,
                                                int lane, WarpScratch& ws) {
   const unsigned full = 0xffffffffu;
@@ -283,16 +311,17 @@ __device__ __forceinline__ float channel_table(const CompState& cs, int K, int c
   float mx = lw;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
-  float e = lane < K ? expf(__fsub_rn(lw, mx)) : 0.f;
+  float e = lane < K ? exp_f(__fsub_rn(lw, mx)) : 0.f;
   float s = e;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(full, s, o));
   if (lane < K) {
     m = comp_mean(cs, ch, r, g);
-    // y = -(e_b - m)/s * log2(e) = be - b * al
-    float c = __fmul_rn(expf(-cs.ls[ch]), 1.4426950408889634f);
-    ws.al[lane] = __fmul_rn(c, __fdiv_rn(2.f, 255.f));
-    ws.be[lane] = __fmul_rn(c, __fadd_rn(m, __fdiv_rn(256.f, 255.f)));
+    const float c = __fmul_rn(exp_f(-cs.ls[ch]), kLog2e);
+    const float al = __fmul_rn(c, 2.f * kInv255);
+    ws.al[lane] = al;
+    ws.be[lane] = __fmul_rn(c, __fadd_rn(m, 256.f * kInv255));
+    ws.rr[lane] = ex2_approx(-al);
     ws.w[lane] = __fdiv_rn(e, s);
   }
   __syncwarp();
@@ -300,13 +329,16 @@ __device__ __forceinline__ float channel_table(const CompState& cs, int K, int c
 #pragma unroll
   for (int q = 0; q < 8; q++) F[q] = 0.f;
   const int b0 = lane * 8;
+  const float fb0 = (float)b0;
   for (int k = 0; k < K; k++) {
-    const float al = ws.al[k], be = ws.be[k], wk = ws.w[k];
+    const float al = ws.al[k], rk = ws.rr[k], wk = ws.w[k];
+    float y = __fmaf_rn(-fb0, al, ws.be[k]);
+    y = fminf(fmaxf(y, -126.f), 126.f);
+    float E = ex2_approx(y);
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-      float y = __fmaf_rn(-(float)(b0 + q), al, be);
-      float sg = rcp_approx(__fadd_rn(1.f, ex2_approx(y)));
-      F[q] = __fmaf_rn(wk, sg, F[q]);
+      if (q) E = __fmul_rn(E, rk);
+      F[q] = __fmaf_rn(wk, rcp_approx(__fadd_rn(1.f, E)), F[q]);
     }
   }
   // quantise and running max

@@ -292,7 +292,9 @@ __device__ __forceinline__ bool tc_wait(TcSmem& t) {
   return ok;
 }
 
-__device__ __forceinline__ float elu_tc(float x) { return x > 0.f ? x : expm1f(x); }
+__device__ __forceinline__ float elu_tc(float x) {
+  return x > 0.f ? x : __fsub_rn(ex2_approx(__fmul_rn(x, 1.4426950408889634f)), 1.f);
+}
 
 // Writes 8 values (columns k0..k0+7) of row r into the BF16 H tile.
 __device__ __forceinline__ void store_h8(uint16_t* H, int r, int k0, int C, const float (&v)[8]) {
@@ -305,10 +307,12 @@ __device__ __forceinline__ void store_h8(uint16_t* H, int r, int k0, int C, cons
 }
 
 // Runs the whole network on the tile in X; P[m][ldP] = head outputs.
-static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t) {
+static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid) {
   const TcPlan pl = tc_plan(d);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane;
+  // a warp whose 32 TMEM lanes hold no valid pixel skips its epilogue
+  const bool live = 32 * (warp & 3) < n_valid;
   const int half = warp >> 2;
   const uint32_t tl = t.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   const int C = d.C, ch = C / 2, c0 = half * ch;
@@ -323,7 +327,7 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t) {
   ok &= tc_wait(t);
 #pragma unroll
   for (int g = 0; g < kMaxC / 16; g++) {
-    if (g < ch / 8) {
+    if (live && g < ch / 8) {
       float v[8];
       tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
 #pragma unroll
@@ -346,7 +350,7 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t) {
     ok &= tc_wait(t);
 #pragma unroll
     for (int g = 0; g < kMaxC / 16; g++) {
-      if (g < ch / 8) {
+      if (live && g < ch / 8) {
         float v[8];
         tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
 #pragma unroll
@@ -362,7 +366,7 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t) {
     ok &= tc_wait(t);
 #pragma unroll
     for (int g = 0; g < kMaxC / 16; g++) {
-      if (g < ch / 8) {
+      if (live && g < ch / 8) {
         float v[8];
         tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
 #pragma unroll
@@ -383,7 +387,7 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t) {
   tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.wh, C, d.NOp);
   ok &= tc_wait(t);
   const int nh = d.NOp / 2, n0 = half * nh;
-  for (int g = 0; g < nh / 8; g++) {
+  for (int g = 0; live && g < nh / 8; g++) {
     float v[8];
     tmem_ld8(tl + (uint32_t)(n0 + 8 * g), v);
     float* o = t.P + (size_t)row * d.ldP + n0 + 8 * g;

@@ -224,11 +224,12 @@ __device__ __forceinline__ void load_weights(const DeviceModel& m, TileSmem& t) 
 
 // gather + network for the slots of the tile; P[m][NOp] lands in t.U0.
 template <int PREC, bool kCoherent>
-__device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* units, TileSmem& t) {
+__device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* units, TileSmem& t,
+                                             int n_valid) {
   if constexpr (PREC == PREC_BF16) {
     tc_gather<kCoherent>(units, t.slots, m.d, t.tc);
     __syncthreads();
-    tc_network(m.d, t.tc);
+    tc_network(m.d, t.tc, n_valid);
   } else {
     gather_f32<kMT, kCoherent>(units, t.slots, m.d.h, t.U0);
     __syncthreads();

@@ -37,7 +37,7 @@ EXPORTS = [
     "nlc_get_weights", "nlc_set_weights", "nlc_weight_hash", "nlc_sync_status", "nlc_set_tuning",
     "nlc_compress_bound", "nlc_compress", "nlc_decompress", "nlc_forward", "nlc_tables",
     "nlc_rans_encode", "nlc_rans_decode", "nlc_train_step", "nlc_loss_grad",
-    "nlc_compress_noalloc",
+    "nlc_compress_noalloc", "nlc_decode_profile",
 ]
 
 
@@ -90,6 +90,7 @@ def load():
             L.nlc_train_step.argtypes = [p, p, i, i, i, f, p, p]
             L.nlc_loss_grad.argtypes = [p, p, i, i, i, p, p, p]
             L.nlc_compress_noalloc.argtypes = [p, p, i, i, i, p, sz, p, p]
+            L.nlc_decode_profile.argtypes = [p, i, p]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -173,6 +174,13 @@ def nlc_weight_hash(ctx):
 def nlc_sync_status(ctx, stream=None):
     """Returns the device status code (0 = OK) and clears it; does not raise."""
     return load().nlc_sync_status(ctx, _stream(stream))
+
+
+def nlc_decode_profile(ctx, enable, read=True):
+    """Enables/disables decoder phase profiling; returns the 8 counters (or None)."""
+    out = np.zeros(8, dtype=np.uint64) if read else None
+    _check(load().nlc_decode_profile(ctx, int(enable), _ptr(out) if read else None))
+    return out
 
 
 def nlc_set_tuning(ctx, px_per_cta, max_ctas=0):
