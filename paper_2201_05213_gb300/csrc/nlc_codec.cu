@@ -485,18 +485,25 @@ cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t
 __global__ void tables_kernel(int K, int NO, const float* __restrict__ params,
                               const uint8_t* __restrict__ pixels, long long n,
                               uint32_t* __restrict__ cum) {
-  __shared__ WarpScratch ws[kWarps];
+  // the codec's 16-lane coding groups, two pixels per warp
+  __shared__ WarpScratch ws[kGroups];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (long long q = (long long)blockIdx.x * kWarps + warp; q < n;
-       q += (long long)gridDim.x * kWarps) {
-    const int v[3] = {pixels[3 * q], pixels[3 * q + 1], pixels[3 * q + 2]};
+  const int half = lane >> 4, gl = lane & (kGW - 1);
+  for (long long q0 = ((long long)blockIdx.x * kWarps + warp) * 2; q0 < n;
+       q0 += (long long)gridDim.x * kWarps * 2) {
+    const long long q = q0 + half;
+    const bool valid = q < n;
+    const long long qe = valid ? q : q0;
+    const int v[3] = {pixels[3 * qe], pixels[3 * qe + 1], pixels[3 * qe + 2]};
+    WarpScratch& g = ws[2 * warp + half];
     CompState cs;
-    comp_init(params + q * NO, K, lane, cs);
+    comp_init<kGW>(params + qe * NO, K, gl, cs);
     for (int ch = 0; ch < 3; ch++) {
-      float mloc = channel_table(cs, K, ch, v[0], v[1], lane, ws[warp]);
-      uint32_t* o = cum + (q * 3 + ch) * 257;
-      for (int b = lane; b < 257; b += 32) o[b] = ws[warp].cum[b];
-      if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], lane);
+      const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, g);
+      uint32_t* o = cum + (qe * 3 + ch) * 257;
+      if (valid)
+        for (int b = gl; b < 257; b += kGW) o[b] = g.cum[b];
+      if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
       __syncwarp();
     }
   }
@@ -546,7 +553,7 @@ __global__ void rans_dec_test_kernel(const uint8_t* __restrict__ in, long long s
   const bool fits = len >= 4 && len <= stride;
   if (!fits) len = 0;
   const uint8_t* base = in + (long long)s * stride + stride - len;
-  WarpRansDec dec;
+  GroupRansDec dec;
   dec.bad = !fits;
   dec.x = kRansL;
   dec.pos = 4;
@@ -557,8 +564,8 @@ __global__ void rans_dec_test_kernel(const uint8_t* __restrict__ in, long long s
   for (long long k = sym_off[s]; k < sym_off[s + 1]; k++) {
     for (int b = lane; b < 257; b += 32) ws[warp].cum[b] = cum[k * 257 + b];
     __syncwarp();
-    dec.prefetch(base, lane);
-    const int v = dec.decode(ws[warp], lane);
+    dec.load_bytes(base);
+    const int v = dec.decode<32>(ws[warp], lane);
     dec.pos += dec.used;
     if (lane == 0) sym[k] = v;
     __syncwarp();

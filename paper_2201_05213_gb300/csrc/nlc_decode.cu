@@ -69,29 +69,59 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
         t.slots[s] = ps;
       }
       __syncthreads();
+      // lane l of warp w fetches the rANS state and next 8 bytes of the warp's
+      // l-th pixel (slot 2w + (l & 1) + 16 (l >> 1)) ahead of the network
+      uint32_t px_x = 0, px_lo = 0, px_hi = 0;
+      unsigned long long px_pos = 0, px_end = 0;
+      {
+        const int sl = 2 * warp + (lane & 1) + kGroups * (lane >> 1);
+        if (sl < n) {
+          const int sid = t.slots[sl].aux;
+          GroupRansDec pd;
+          pd.x = ld_cg_u32(a.st_x + sid);
+          pd.pos = ld_cg_u64(a.st_pos + sid);
+          pd.end = a.st_end[sid];
+          pd.load_bytes(a.in);
+          px_x = pd.x;
+          px_pos = pd.pos;
+          px_end = pd.end;
+          px_lo = pd.lo;
+          px_hi = pd.hi;
+        }
+      }
       if (prof) { tn = clock64(); ph1 += tn - tc; tc = tn; tiles++; }
       tile_network<PREC, true>(a.m, a.units, t, n);
       if (prof) { tn = clock64(); ph2 += tn - tc; tc = tn; }
-      for (int s = warp; s < n; s += kWarps) {
-        const PixSlot ps = t.slots[s];
+      // Per-pixel coding: each warp codes two pixels at once, one per 16-lane
+      // group (group 2w + half takes slots 2w + half + 16 j).
+      const int half = lane >> 4, gl = lane & (kGW - 1);
+      for (int j = 0; 2 * warp + kGroups * j < n; j++) {
+        const int s = 2 * warp + half + kGroups * j;
+        const bool valid = s < n;
+        const int se = valid ? s : s - 1;  // an idle group shadows its neighbour
+        const int src = 2 * j + half;
+        GroupRansDec dec;
+        dec.x = __shfl_sync(0xffffffffu, px_x, src);
+        dec.pos = __shfl_sync(0xffffffffu, px_pos, src);
+        dec.end = __shfl_sync(0xffffffffu, px_end, src);
+        dec.lo = __shfl_sync(0xffffffffu, px_lo, src);
+        dec.hi = __shfl_sync(0xffffffffu, px_hi, src);
+        dec.used = 0;
+        dec.bad = false;
+        const PixSlot ps = t.slots[se];
         const Unit U = a.units[ps.unit];
         const int sid = ps.aux;
-        WarpRansDec dec;
-        dec.x = ld_cg_u32(a.st_x + sid);
-        dec.pos = ld_cg_u64(a.st_pos + sid);
-        dec.end = a.st_end[sid];
-        dec.bad = false;
-        dec.prefetch(a.in, lane);
+        WarpScratch& ws = t.ws[2 * warp + half];
         CompState cs;
-        comp_init(t.U0 + (size_t)s * ldP, K, lane, cs);
+        comp_init<kGW>(t.U0 + (size_t)se * ldP, K, gl, cs);
         int v[3] = {0, 0, 0};
         for (int ch = 0; ch < 3; ch++) {
-          float mloc = channel_table(cs, K, ch, v[0], v[1], lane, t.ws[warp]);
-          v[ch] = dec.decode(t.ws[warp], lane);
-          if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], lane);
+          const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, ws);
+          v[ch] = dec.decode<kGW>(ws, lane);
+          if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
           __syncwarp();
         }
-        if (lane == 0) {
+        if (gl == 0 && valid) {
           uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
           px[0] = (uint8_t)v[0];
           px[1] = (uint8_t)v[1];

@@ -37,20 +37,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     tile_network<PREC, false>(m, units, t, (int)min((long long)MT, n_px - tile * MT));
-    for (int s = warp; s < MT; s += kWarps) {
-      const PixSlot ps = t.slots[s];
-      if (ps.unit < 0) continue;
+    // two pixels per warp, one per 16-lane coding group (as in the decoder)
+    const int half = lane >> 4, gl = lane & (kGW - 1);
+    for (int j = 0; 2 * warp + kGroups * j < MT; j++) {
+      const int s = 2 * warp + half + kGroups * j;
+      const bool valid = t.slots[s].unit >= 0;
+      if (!__any_sync(0xffffffffu, valid)) break;
+      const int se = valid ? s : (s ^ 1);  // an idle group shadows its neighbour
+      const PixSlot ps = t.slots[se];
       const Unit U = units[ps.unit];
       const uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
       const int v[3] = {px[0], px[1], px[2]};
       const long long q = tile * MT + s;
+      WarpScratch& ws = t.ws[2 * warp + half];
       CompState cs;
-      comp_init(t.U0 + (size_t)s * ldP, K, lane, cs);
+      comp_init<kGW>(t.U0 + (size_t)se * ldP, K, gl, cs);
       for (int ch = 0; ch < 3; ch++) {
-        float mloc = channel_table(cs, K, ch, v[0], v[1], lane, t.ws[warp]);
-        const uint32_t c0 = t.ws[warp].cum[v[ch]], c1 = t.ws[warp].cum[v[ch] + 1];
-        if (lane == 0) stage[3 * q + ch] = c0 | ((c1 - c0) << 16);
-        if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], lane);
+        const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, ws);
+        const uint32_t c0 = ws.cum[v[ch]], c1 = ws.cum[v[ch] + 1];
+        if (gl == 0 && valid) stage[3 * q + ch] = c0 | ((c1 - c0) << 16);
+        if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
         __syncwarp();
       }
     }

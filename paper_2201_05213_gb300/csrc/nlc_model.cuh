@@ -247,13 +247,37 @@ __device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
   return __fadd_rn(__fsub_rn(-softplus_f(-a), softplus_f(b)), lme);
 }
 
-// Per-warp scratch of the CDF stage.
+// Scratch of one coding group (a warp, or half a warp) in the CDF stage.
 struct alignas(16) WarpScratch {
   float al[kMaxK], be[kMaxK], w[kMaxK], rr[kMaxK];
   uint32_t cum[260];
 };
 static_assert(sizeof(WarpScratch) % 16 == 0, "WarpScratch keeps 16-byte alignment in arrays");
 
+// ---------------------------------------------------------------------
+// Coding groups.  One pixel's channel tables are built by a group of GW
+// lanes (GW = 32: a whole warp; GW = 16: half a warp, so that a warp codes
+// two pixels at once).  Lane gl of a group owns the BPL = 256/GW boundaries
+// b = BPL gl .. BPL gl + BPL - 1; lanes gl < K also hold component gl.  All
+// group reductions are xor butterflies, which give the same value in every
+// lane of the group.  The encoder and the decoder use the same GW.
+// ---------------------------------------------------------------------
+template <int GW>
+__device__ __forceinline__ float grp_max(float v) {
+#pragma unroll
+  for (int o = GW / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o, GW));
+  return v;
+}
+template <int GW>
+__device__ __forceinline__ float grp_sum(float v) {
+#pragma unroll
+  for (int o = GW / 2; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o, GW));
+  return v;
+}
+template <int GW>
+__device__ __forceinline__ unsigned grp_mask(int lane) {
+  return GW == 32 ? 0xffffffffu : (0xFFFFu << (lane & 16));
+}
 
 // Per-pixel mixture state held by lane k (< K) for component k.
 struct CompState {
@@ -261,26 +285,21 @@ struct CompState {
   float mu[3], ls[3], co[3];
 };
 
-__device__ __forceinline__ void comp_init(const float* P, int K, int lane, CompState& cs) {
-  const unsigned full = 0xffffffffu;
-  float logit = lane < K ? P[lane] : -INFINITY;
-  float mx = logit;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
-  float e = lane < K ? exp_f(__fsub_rn(logit, mx)) : 0.f;
-  float s = e;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(full, s, o));
-  // the xor-butterfly sum is the same expression tree in every lane
-  float lse = __fadd_rn(mx, log_f(s));
+template <int GW = 32>
+__device__ __forceinline__ void comp_init(const float* P, int K, int gl, CompState& cs) {
+  const float logit = gl < K ? P[gl] : -INFINITY;
+  const float mx = grp_max<GW>(logit);
+  const float e = gl < K ? exp_f(__fsub_rn(logit, mx)) : 0.f;
+  const float s = grp_sum<GW>(e);
+  const float lse = __fadd_rn(mx, log_f(s));
   cs.logpi = __fsub_rn(logit, lse);
   cs.lw = cs.logpi;
-  if (lane < K) {
+  if (gl < K) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      cs.mu[c] = P[K + c * K + lane];
-      cs.ls[c] = fmaxf(P[4 * K + c * K + lane], -7.f);
-      cs.co[c] = tanhf(P[7 * K + c * K + lane]);
+      cs.mu[c] = P[K + c * K + gl];
+      cs.ls[c] = fmaxf(P[4 * K + c * K + gl], -7.f);
+      cs.co[c] = tanhf(P[7 * K + c * K + gl]);
     }
   }
 }
@@ -293,98 +312,102 @@ __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, i
   return __fadd_rn(__fadd_rn(cs.mu[2], __fmul_rn(cs.co[1], xr)), __fmul_rn(cs.co[2], xg));
 }
 
-// Builds cum[0..256] of channel ch in ws.cum (whole warp).  Returns the
+// Builds cum[0..256] of channel ch in ws.cum (whole group).  Returns the
 // location of the lane's component (for the posterior update).
 //
-// Lane l owns the boundaries b = 8l..8l+7.  With
-// y_k(b) = -(e_b - m_k)/s_k log2(e) = be_k - b al_k, component k's logistic
-// is 1/(1 + 2^y): one ex2 at the lane's first boundary, then 2^y of the next
-// boundary by one multiply with 2^-al_k, and one rcp per boundary.  The sum
-// runs over k in a fixed order, so F(b) is the same expression of the pixel's
-// parameters in every kernel.
+// With y_k(b) = -(e_b - m_k)/s_k log2(e) = be_k - b al_k, component k's
+// logistic is 1/(1 + 2^y): one ex2 at the lane's first boundary, then 2^y of
+// the next boundary by one multiply with 2^-al_k, and one rcp per boundary.
+// The sum runs over k in a fixed order, so F(b) is the same expression of the
+// pixel's parameters in every kernel that uses the same GW.
+template <int GW>
 __device__ __forceinline__ float channel_table(const CompState& cs, int K, int ch, int r, int g,
-                                               int lane, WarpScratch& ws) {
-  const unsigned full = 0xffffffffu;
+                                               int gl, WarpScratch& ws) {
+  constexpr int BPL = 256 / GW;
   float m = 0.f;
   // component weights: softmax of the running log weights
-  float lw = lane < K ? cs.lw : -INFINITY;
-  float mx = lw;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(full, mx, o));
-  float e = lane < K ? exp_f(__fsub_rn(lw, mx)) : 0.f;
-  float s = e;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(full, s, o));
-  if (lane < K) {
+  const float lw = gl < K ? cs.lw : -INFINITY;
+  const float mx = grp_max<GW>(lw);
+  const float e = gl < K ? exp_f(__fsub_rn(lw, mx)) : 0.f;
+  const float s = grp_sum<GW>(e);
+  if (gl < K) {
     m = comp_mean(cs, ch, r, g);
     const float c = __fmul_rn(exp_f(-cs.ls[ch]), kLog2e);
     const float al = __fmul_rn(c, 2.f * kInv255);
-    ws.al[lane] = al;
-    ws.be[lane] = __fmul_rn(c, __fadd_rn(m, 256.f * kInv255));
-    ws.rr[lane] = ex2_approx(-al);
-    ws.w[lane] = __fdiv_rn(e, s);
+    ws.al[gl] = al;
+    ws.be[gl] = __fmul_rn(c, __fadd_rn(m, 256.f * kInv255));
+    ws.rr[gl] = ex2_approx(-al);
+    ws.w[gl] = __fdiv_rn(e, s);
   }
   __syncwarp();
-  float F[8];
+  float F[BPL];
 #pragma unroll
-  for (int q = 0; q < 8; q++) F[q] = 0.f;
-  const int b0 = lane * 8;
+  for (int q = 0; q < BPL; q++) F[q] = 0.f;
+  const int b0 = gl * BPL;
   const float fb0 = (float)b0;
+  // Chains of 8 boundaries restart from an exact ex2: with |y| clamped at
+  // 126 and al <= 12.4 (log-scale >= -7), seven steps from a clamped start
+  // stay beyond |y| = 39, where the logistic is 0 or 1 to within 2^-39.
   for (int k = 0; k < K; k++) {
-    const float al = ws.al[k], rk = ws.rr[k], wk = ws.w[k];
-    float y = __fmaf_rn(-fb0, al, ws.be[k]);
-    y = fminf(fmaxf(y, -126.f), 126.f);
-    float E = ex2_approx(y);
+    const float al = ws.al[k], rk = ws.rr[k], wk = ws.w[k], be = ws.be[k];
+    float E = 0.f;
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-      if (q) E = __fmul_rn(E, rk);
+    for (int q = 0; q < BPL; q++) {
+      if ((q & 7) == 0) {
+        float y = __fmaf_rn(-(fb0 + (float)q), al, be);
+        y = fminf(fmaxf(y, -126.f), 126.f);
+        E = ex2_approx(y);
+      } else {
+        E = __fmul_rn(E, rk);
+      }
       F[q] = __fmaf_rn(wk, rcp_approx(__fadd_rn(1.f, E)), F[q]);
     }
   }
-  // quantise and running max
+  // quantise, running max within the lane, then across the group
   int Q = 0;
-  int qv[8];
 #pragma unroll
-  for (int q = 0; q < 8; q++) {
-    int b = b0 + q;
+  for (int q = 0; q < BPL; q++) {
     int v = __float2int_rn(__fmul_rn(65280.f, F[q]));
     v = v < 0 ? 0 : (v > kMq ? kMq : v);
-    if (b == 0) v = 0;
+    if (b0 + q == 0) v = 0;
     Q = v > Q ? v : Q;
-    qv[q] = Q;
+    F[q] = __int_as_float(Q);  // reuse the registers for the running max
   }
-  int pre = Q;  // inclusive max over lanes <= lane
+  int pre = Q;  // inclusive max over group lanes <= gl
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(full, pre, o);
-    if (lane >= o) pre = t > pre ? t : pre;
+  for (int o = 1; o < GW; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, pre, o, GW);
+    if (gl >= o) pre = t > pre ? t : pre;
   }
-  int excl = __shfl_up_sync(full, pre, 1);
-  if (lane == 0) excl = 0;
+  int excl = __shfl_up_sync(0xffffffffu, pre, 1, GW);
+  if (gl == 0) excl = 0;
 #pragma unroll
-  for (int q = 0; q < 8; q++) {
-    int v = qv[q] > excl ? qv[q] : excl;
-    ws.cum[b0 + q] = (uint32_t)(v + b0 + q);
+  for (int q = 0; q < BPL; q++) {
+    const int qv = __float_as_int(F[q]);
+    ws.cum[b0 + q] = (uint32_t)((qv > excl ? qv : excl) + b0 + q);
   }
-  if (lane == 0) ws.cum[256] = 65536u;
+  if (gl == 0) ws.cum[256] = 65536u;
   __syncwarp();
   return m;
 }
 
 // Symbol s with cum_s <= slot < cum_{s+1} (cum strictly increasing).
+template <int GW>
 __device__ __forceinline__ int table_search(const WarpScratch& ws, uint32_t slot, int lane) {
+  constexpr int BPL = 256 / GW;
+  const int gl = lane & (GW - 1);
   int cnt = 0;
 #pragma unroll
-  for (int q = 0; q < 8; q++) {
-    int b = lane * 8 + q;
+  for (int q = 0; q < BPL; q++) {
+    const int b = gl * BPL + q;
     cnt += (b >= 1 && ws.cum[b] <= slot) ? 1 : 0;
   }
-  return __reduce_add_sync(0xffffffffu, cnt);
+  return __reduce_add_sync(grp_mask<GW>(lane), cnt);
 }
 
 // Posterior update after channel ch took value v (lanes < K).
-__device__ __forceinline__ void comp_observe(CompState& cs, int K, int ch, float m, int v, int lane) {
-  if (lane < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, cs.ls[ch], v));
+__device__ __forceinline__ void comp_observe(CompState& cs, int K, int ch, float m, int v, int gl) {
+  if (gl < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, cs.ls[ch], v));
 }
 
 }  // namespace nlc

@@ -185,6 +185,41 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   v[7] = __uint_as_float(r7);
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane (one load, one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// The columns c0 .. c0 + ch - 1 (ch = 8, 16, 24 or 32) of this thread's lane.
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int ch, float (&v)[32]) {
+  if (ch == 32) {
+    tmem_ld32(taddr, v);
+  } else {
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      if (g < ch / 8) {
+        float u[8];
+        tmem_ld8(taddr + (uint32_t)(8 * g), u);
+#pragma unroll
+        for (int e = 0; e < 8; e++) v[8 * g + e] = u[e];
+      }
+    }
+  }
+}
+
 // --- setup / teardown -------------------------------------------------------
 __device__ __forceinline__ void tc_setup(TcSmem& t) {
   if (threadIdx.x == 0) {
@@ -234,38 +269,51 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // X(m, k) = 2v - 255 for feature k = 3p + c of tap p, 0 outside the unit,
 // for k >= F and for empty slots.  Each thread writes 16-byte chunks.
 template <bool kCoherent>
-__device__ __noinline__ void tc_gather(const Unit* units, const PixSlot* slots, const Dims& d, TcSmem& t) {
-  const int Fp = d.Fp, F = d.F, h = d.h, w2 = 2 * h + 1;
-  const int nchunk = kTcM * (Fp / 8);
-  for (int it = threadIdx.x; it < nchunk; it += blockDim.x) {
-    const int m = it % kTcM, kb = it / kTcM;
-    const PixSlot s = slots[m];
-    float v[8];
+__device__ __noinline__ void tc_gather(const Unit* units, const PixSlot* slots, const Dims& d,
+                                       TcSmem& t, int n_valid) {
+  // (pixel, tap) pairs of the valid rows; each thread issues all its context
+  // loads before any shared-memory store.  Rows >= n_valid are left as they
+  // are: tensor-core rows are independent and their outputs are not read.
+  constexpr int kMaxPairs = (kTcM * 2 * kMaxH * (kMaxH + 1) + kThreads - 1) / kThreads;
+  const int Fp = d.Fp, F = d.F, h = d.h, w2 = 2 * h + 1, ntap = 2 * h * (h + 1);
+  const int npairs = n_valid * ntap;
+  uint32_t val[kMaxPairs];
 #pragma unroll
-    for (int e = 0; e < 8; e++) v[e] = 0.f;
-    if (s.unit >= 0) {
+  for (int r = 0; r < kMaxPairs; r++) {
+    const int it = threadIdx.x + r * kThreads;
+    uint32_t v = 0;
+    if (it < npairs) {
+      const int m = it / ntap, p = it - m * ntap;
+      const PixSlot s = slots[m];
       const Unit u = units[s.unit];
-#pragma unroll
-      for (int e = 0; e < 8; e++) {
-        const int k = kb * 8 + e;
-        if (k < F) {
-          const int p = k / 3, c = k - 3 * p;
-          const int ii = s.i + p / w2 - h, jj = s.j + p % w2 - h;
-          if (ii >= 0 && ii < u.Hu && jj >= 0 && jj < u.Wu) {
-            const uint8_t* px =
-                u.img + ((long long)(u.y0 + ii) * u.img_W + (u.x0 + jj)) * 3 + c;
-            const int b = kCoherent ? (int)ld_cg_u8(px) : (int)*px;
-            v[e] = (float)(2 * b - 255);
-          }
-        }
+      const int ii = s.i + p / w2 - h, jj = s.j + p % w2 - h;
+      if (ii >= 0 && ii < u.Hu && jj >= 0 && jj < u.Wu) {
+        const uint8_t* px = u.img + ((long long)(u.y0 + ii) * u.img_W + (u.x0 + jj)) * 3;
+        const uint32_t b0 = kCoherent ? ld_cg_u8(px) : px[0];
+        const uint32_t b1 = kCoherent ? ld_cg_u8(px + 1) : px[1];
+        const uint32_t b2 = kCoherent ? ld_cg_u8(px + 2) : px[2];
+        v = b0 | (b1 << 8) | (b2 << 16) | (1u << 24);
       }
     }
-    uint4 q;
-    q.x = pack_bf16(v[0], v[1]);
-    q.y = pack_bf16(v[2], v[3]);
-    q.z = pack_bf16(v[4], v[5]);
-    q.w = pack_bf16(v[6], v[7]);
-    *reinterpret_cast<uint4*>(t.X + umma_off(m, kb * 8, Fp)) = q;
+    val[r] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < kMaxPairs; r++) {
+    const int it = threadIdx.x + r * kThreads;
+    if (it < npairs) {
+      const int m = it / ntap, p = it - m * ntap;
+      const uint32_t v = val[r];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float x = (v >> 24) ? (float)(2 * (int)((v >> (8 * c)) & 0xFFu) - 255) : 0.f;
+        t.X[umma_off(m, 3 * p + c, Fp)] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+      }
+    }
+  }
+  const int npad = Fp - F;
+  for (int it = threadIdx.x; it < n_valid * npad; it += kThreads) {
+    const int m = it / npad, k = F + it % npad;
+    t.X[umma_off(m, k, Fp)] = 0;
   }
 }
 
@@ -325,17 +373,20 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_v
   __syncthreads();
   tc_issue(t, (uint32_t)pl.p, (uint32_t)pl.w0, d.Fp, C);
   ok &= tc_wait(t);
+  if (live) {
+    float v[32];
+    tmem_ld_cols(tl + (uint32_t)c0, ch, v);
 #pragma unroll
-  for (int g = 0; g < kMaxC / 16; g++) {
-    if (live && g < ch / 8) {
-      float v[8];
-      tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
+    for (int g = 0; g < kMaxC / 16; g++) {
+      if (g < ch / 8) {
+        float u[8];
 #pragma unroll
-      for (int e = 0; e < 8; e++) {
-        a[8 * g + e] = __fadd_rn(v[e], b0[c0 + 8 * g + e]);
-        v[e] = elu_tc(a[8 * g + e]);
+        for (int e = 0; e < 8; e++) {
+          a[8 * g + e] = __fadd_rn(v[8 * g + e], b0[c0 + 8 * g + e]);
+          u[e] = elu_tc(a[8 * g + e]);
+        }
+        store_h8(t.H, row, c0 + 8 * g, C, u);
       }
-      store_h8(t.H, row, c0 + 8 * g, C, v);
     }
   }
   fence_before_sync();
@@ -348,14 +399,17 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_v
     // hidden = ELU(H W1^T + b1)
     tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w1[r], C, C);
     ok &= tc_wait(t);
+    if (live) {
+      float v[32];
+      tmem_ld_cols(tl + (uint32_t)c0, ch, v);
 #pragma unroll
-    for (int g = 0; g < kMaxC / 16; g++) {
-      if (live && g < ch / 8) {
-        float v[8];
-        tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
+      for (int g = 0; g < kMaxC / 16; g++) {
+        if (g < ch / 8) {
+          float u[8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) v[e] = elu_tc(__fadd_rn(v[e], b1[c0 + 8 * g + e]));
-        store_h8(t.H, row, c0 + 8 * g, C, v);
+          for (int e = 0; e < 8; e++) u[e] = elu_tc(__fadd_rn(v[8 * g + e], b1[c0 + 8 * g + e]));
+          store_h8(t.H, row, c0 + 8 * g, C, u);
+        }
       }
     }
     fence_before_sync();
@@ -364,17 +418,20 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_v
     // a += H W2^T + b2, H = ELU(a)
     tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w2[r], C, C);
     ok &= tc_wait(t);
+    if (live) {
+      float v[32];
+      tmem_ld_cols(tl + (uint32_t)c0, ch, v);
 #pragma unroll
-    for (int g = 0; g < kMaxC / 16; g++) {
-      if (live && g < ch / 8) {
-        float v[8];
-        tmem_ld8(tl + (uint32_t)(c0 + 8 * g), v);
+      for (int g = 0; g < kMaxC / 16; g++) {
+        if (g < ch / 8) {
+          float u[8];
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-          a[8 * g + e] = __fadd_rn(a[8 * g + e], __fadd_rn(v[e], b2[c0 + 8 * g + e]));
-          v[e] = elu_tc(a[8 * g + e]);
+          for (int e = 0; e < 8; e++) {
+            a[8 * g + e] = __fadd_rn(a[8 * g + e], __fadd_rn(v[8 * g + e], b2[c0 + 8 * g + e]));
+            u[e] = elu_tc(a[8 * g + e]);
+          }
+          store_h8(t.H, row, c0 + 8 * g, C, u);
         }
-        store_h8(t.H, row, c0 + 8 * g, C, v);
       }
     }
     fence_before_sync();

@@ -92,28 +92,42 @@ __device__ __forceinline__ int front_scan(const Unit* __restrict__ units, int n_
 // rANS: warp-level decoder of one stream position and the per-stream
 // encoder (byte-wise renormalisation, state in [2^23, 2^31)).
 // ---------------------------------------------------------------------
-struct WarpRansDec {
+// Coding groups of the codec kernels: 16 lanes (half a warp) per pixel.
+constexpr int kGW = 16;
+constexpr int kGroups = kThreads / kGW;
+
+// Decoder of one rANS stream position, held uniformly by a coding group.
+// The next 8 stream bytes (a pixel consumes at most 6) are prefetched into
+// two registers.
+struct GroupRansDec {
   uint32_t x;
   unsigned long long pos, end;
-  uint32_t byte;
+  uint32_t lo, hi;  // bytes pos .. pos+7, little-endian packed
   int used;
   bool bad;
 
-  __device__ __forceinline__ void prefetch(const uint8_t* base, int lane) {
-    byte = 0;
-    unsigned long long p = pos + (unsigned long long)lane;
-    if (lane < 8 && p < end) byte = base[p];
+  __device__ __forceinline__ void load_bytes(const uint8_t* base) {
+    lo = hi = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const unsigned long long p = pos + (unsigned long long)k;
+      const uint32_t v = p < end ? (uint32_t)base[p] : 0u;
+      if (k < 4) lo |= v << (8 * k);
+      else hi |= v << (8 * (k - 4));
+    }
     used = 0;
   }
   // slot = x mod 2^16, symbol s with cum_s <= slot < cum_{s+1},
   // x = freq (x >> 16) + slot - cum_s, then shift bytes in while x < 2^23.
+  template <int GW>
   __device__ __forceinline__ int decode(const WarpScratch& ws, int lane) {
     const uint32_t slot = x & 0xFFFFu;
-    const int s = table_search(ws, slot, lane);
+    const int s = table_search<GW>(ws, slot, lane);
     const uint32_t c0 = ws.cum[s], c1 = ws.cum[s + 1];
     x = (c1 - c0) * (x >> 16) + slot - c0;
     for (int it = 0; it < 3 && x < kRansL; it++) {
-      uint32_t bt = __shfl_sync(0xffffffffu, byte, used & 7);
+      const uint32_t bt = used < 4 ? (lo >> (8 * used)) & 0xFFu
+                                   : used < 8 ? (hi >> (8 * (used - 4))) & 0xFFu : 0u;
       if (used >= 8 || pos + (unsigned long long)used >= end) bad = true;
       x = (x << 8) | bt;
       used++;
@@ -172,7 +186,7 @@ __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre) {
     bytes = (size_t)pl.end * 4;
   }
   bytes = (bytes + 15) & ~(size_t)15;
-  bytes += sizeof(WarpScratch) * kWarps;
+  bytes += sizeof(WarpScratch) * kGroups;
   bytes += sizeof(PixSlot) * kTileMax;
   bytes += sizeof(long long) * 33;
   bytes += sizeof(int) * (n_pre + 1 + 4);
@@ -198,7 +212,7 @@ __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, in
   }
   off = (off + 15) & ~(size_t)15;
   t.ws = reinterpret_cast<WarpScratch*>(smem + off);
-  off += sizeof(WarpScratch) * kWarps;
+  off += sizeof(WarpScratch) * kGroups;
   t.slots = reinterpret_cast<PixSlot*>(smem + off);
   off += sizeof(PixSlot) * kTileMax;
   t.sh = reinterpret_cast<long long*>(smem + off);
@@ -227,7 +241,7 @@ template <int PREC, bool kCoherent>
 __device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* units, TileSmem& t,
                                              int n_valid) {
   if constexpr (PREC == PREC_BF16) {
-    tc_gather<kCoherent>(units, t.slots, m.d, t.tc);
+    tc_gather<kCoherent>(units, t.slots, m.d, t.tc, n_valid);
     __syncthreads();
     tc_network(m.d, t.tc, n_valid);
   } else {
