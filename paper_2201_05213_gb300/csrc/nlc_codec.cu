@@ -502,7 +502,7 @@ __global__ void tables_kernel(int K, int NO, const float* __restrict__ params,
       const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, g);
       uint32_t* o = cum + (qe * 3 + ch) * 257;
       if (valid)
-        for (int b = gl; b < 257; b += kGW) o[b] = g.cum[b];
+        for (int b = gl; b < 257; b += kGW) o[b] = cum_at<kGW>(g, b);
       if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
       __syncwarp();
     }
@@ -562,7 +562,7 @@ __global__ void rans_dec_test_kernel(const uint8_t* __restrict__ in, long long s
     dec.x = ((uint32_t)base[0] << 24) | ((uint32_t)base[1] << 16) | ((uint32_t)base[2] << 8) |
             (uint32_t)base[3];
   for (long long k = sym_off[s]; k < sym_off[s + 1]; k++) {
-    for (int b = lane; b < 257; b += 32) ws[warp].cum[b] = cum[k * 257 + b];
+    for (int b = lane; b < 256; b += 32) ws[warp].cum[cum_pos<32>(b)] = cum[k * 257 + b];
     __syncwarp();
     dec.load_bytes(base);
     const int v = dec.decode<32>(ws[warp], lane);

@@ -25,6 +25,64 @@ struct DecodeArgs {
   unsigned long long* prof;  // optional per-phase cycle counters
 };
 
+// Slot of the warp's l-th pixel when coding groups have GW lanes
+// (32 / GW groups per warp, group g of warp w takes slots g + 32/GW (w + 8 j)).
+template <int GW>
+__device__ __forceinline__ int group_slot(int warp, int l) {
+  constexpr int gpw = 32 / GW;
+  return gpw * warp + (l % gpw) + kWarps * gpw * (l / gpw);
+}
+
+// Codes the tile's pixels: per pixel, the R, G|r, B|r,g tables and one rANS
+// symbol each.  pd holds (in lane l) the prefetched stream state of the
+// warp's l-th pixel.
+template <int GW>
+__device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, int n,
+                                       const GroupRansDec& pd) {
+  constexpr int gpw = 32 / GW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / GW, gl = lane % GW;
+  const int K = a.m.d.K, ldP = a.m.d.ldP;
+  for (int j = 0; gpw * warp + kWarps * gpw * j < n; j++) {
+    const int s = gpw * warp + grp + kWarps * gpw * j;
+    const bool valid = s < n;
+    const int se = valid ? s : s - 1;  // an idle group shadows its neighbour
+    const int src = gpw * j + grp;
+    GroupRansDec dec;
+    dec.x = __shfl_sync(0xffffffffu, pd.x, src);
+    dec.pos = __shfl_sync(0xffffffffu, pd.pos, src);
+    dec.end = __shfl_sync(0xffffffffu, pd.end, src);
+    dec.lo = __shfl_sync(0xffffffffu, pd.lo, src);
+    dec.hi = __shfl_sync(0xffffffffu, pd.hi, src);
+    dec.used = 0;
+    dec.bad = false;
+    const PixSlot ps = t.slots[se];
+    const Unit U = a.units[ps.unit];
+    const int sid = ps.aux;
+    WarpScratch& ws = t.ws[gpw * warp + grp];
+    CompState cs;
+    comp_init<GW>(t.U0 + (size_t)se * ldP, K, gl, cs);
+    int v[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ch++) {
+      const float mloc = channel_table<GW>(cs, K, ch, v[0], v[1], gl, ws);
+      v[ch] = dec.decode<GW>(ws, lane);
+      if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
+      __syncwarp();
+    }
+    if (gl == 0 && valid) {
+      uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
+      px[0] = (uint8_t)v[0];
+      px[1] = (uint8_t)v[1];
+      px[2] = (uint8_t)v[2];
+      const unsigned long long np = dec.pos + (unsigned long long)dec.used;
+      a.st_x[sid] = dec.x;
+      a.st_pos[sid] = np;
+      const bool last = a.layout == 1 ? (ps.j == U.Wu - 1) : (ps.i == U.Hu - 1 && ps.j == U.Wu - 1);
+      if (dec.bad || (last && (dec.x != kRansL || np != dec.end))) set_status(a.status, ST_CORRUPT);
+    }
+  }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -36,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
   __syncthreads();
   constexpr int MT = tile_size<PREC>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int K = d.K, ldP = d.ldP, h = d.h;
+  const int h = d.h;
   unsigned my_gen = 0;
   const unsigned G = gridDim.x;
   // phase cycles of thread 0: front scan, slot fill, gather + network,
@@ -69,72 +127,30 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
         t.slots[s] = ps;
       }
       __syncthreads();
-      // lane l of warp w fetches the rANS state and next 8 bytes of the warp's
-      // l-th pixel (slot 2w + (l & 1) + 16 (l >> 1)) ahead of the network
-      uint32_t px_x = 0, px_lo = 0, px_hi = 0;
-      unsigned long long px_pos = 0, px_end = 0;
+      // A CTA with at most one pixel per warp codes with whole warps (lower
+      // latency per pixel); otherwise two pixels per warp.  Both give the
+      // same tables (see channel_table).  Lane l of warp w fetches the rANS
+      // state and next 8 bytes of the warp's l-th pixel ahead of the network.
+      const bool wide = n <= kWarps;
+      GroupRansDec pd;
+      pd.x = 0;
+      pd.pos = pd.end = 0;
+      pd.lo = pd.hi = 0;
       {
-        const int sl = 2 * warp + (lane & 1) + kGroups * (lane >> 1);
+        const int sl = wide ? group_slot<32>(warp, lane) : group_slot<kGW>(warp, lane);
         if (sl < n) {
           const int sid = t.slots[sl].aux;
-          GroupRansDec pd;
           pd.x = ld_cg_u32(a.st_x + sid);
           pd.pos = ld_cg_u64(a.st_pos + sid);
           pd.end = a.st_end[sid];
           pd.load_bytes(a.in);
-          px_x = pd.x;
-          px_pos = pd.pos;
-          px_end = pd.end;
-          px_lo = pd.lo;
-          px_hi = pd.hi;
         }
       }
       if (prof) { tn = clock64(); ph1 += tn - tc; tc = tn; tiles++; }
       tile_network<PREC, true>(a.m, a.units, t, n);
       if (prof) { tn = clock64(); ph2 += tn - tc; tc = tn; }
-      // Per-pixel coding: each warp codes two pixels at once, one per 16-lane
-      // group (group 2w + half takes slots 2w + half + 16 j).
-      const int half = lane >> 4, gl = lane & (kGW - 1);
-      for (int j = 0; 2 * warp + kGroups * j < n; j++) {
-        const int s = 2 * warp + half + kGroups * j;
-        const bool valid = s < n;
-        const int se = valid ? s : s - 1;  // an idle group shadows its neighbour
-        const int src = 2 * j + half;
-        GroupRansDec dec;
-        dec.x = __shfl_sync(0xffffffffu, px_x, src);
-        dec.pos = __shfl_sync(0xffffffffu, px_pos, src);
-        dec.end = __shfl_sync(0xffffffffu, px_end, src);
-        dec.lo = __shfl_sync(0xffffffffu, px_lo, src);
-        dec.hi = __shfl_sync(0xffffffffu, px_hi, src);
-        dec.used = 0;
-        dec.bad = false;
-        const PixSlot ps = t.slots[se];
-        const Unit U = a.units[ps.unit];
-        const int sid = ps.aux;
-        WarpScratch& ws = t.ws[2 * warp + half];
-        CompState cs;
-        comp_init<kGW>(t.U0 + (size_t)se * ldP, K, gl, cs);
-        int v[3] = {0, 0, 0};
-        for (int ch = 0; ch < 3; ch++) {
-          const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, ws);
-          v[ch] = dec.decode<kGW>(ws, lane);
-          if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
-          __syncwarp();
-        }
-        if (gl == 0 && valid) {
-          uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
-          px[0] = (uint8_t)v[0];
-          px[1] = (uint8_t)v[1];
-          px[2] = (uint8_t)v[2];
-          const unsigned long long np = dec.pos + (unsigned long long)dec.used;
-          a.st_x[sid] = dec.x;
-          a.st_pos[sid] = np;
-          const bool last = a.layout == 1 ? (ps.j == U.Wu - 1)
-                                          : (ps.i == U.Hu - 1 && ps.j == U.Wu - 1);
-          if (dec.bad || (last && (dec.x != kRansL || np != dec.end)))
-            set_status(a.status, ST_CORRUPT);
-        }
-      }
+      if (wide) code_tile<32>(a, t, n, pd);
+      else code_tile<kGW>(a, t, n, pd);
       __syncthreads();
       if (prof) { tn = clock64(); ph3 += tn - tc; tc = tn; }
     }

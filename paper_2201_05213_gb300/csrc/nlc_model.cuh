@@ -248,9 +248,10 @@ __device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
 }
 
 // Scratch of one coding group (a warp, or half a warp) in the CDF stage.
+// cum holds cum_0 .. cum_255 lane-interleaved (see cum_pos); cum_256 = 2^16.
 struct alignas(16) WarpScratch {
   float al[kMaxK], be[kMaxK], w[kMaxK], rr[kMaxK];
-  uint32_t cum[260];
+  uint32_t cum[256];
 };
 static_assert(sizeof(WarpScratch) % 16 == 0, "WarpScratch keeps 16-byte alignment in arrays");
 
@@ -277,6 +278,19 @@ __device__ __forceinline__ float grp_sum(float v) {
 template <int GW>
 __device__ __forceinline__ unsigned grp_mask(int lane) {
   return GW == 32 ? 0xffffffffu : (0xFFFFu << (lane & 16));
+}
+
+// Position of cum_b (b < 256) in WarpScratch::cum for groups of GW lanes:
+// lane gl's boundaries b = BPL gl + q sit at q GW + gl, so the group's
+// stores and loads of one q hit consecutive banks.
+template <int GW>
+__device__ __forceinline__ int cum_pos(int b) {
+  constexpr int BPL = 256 / GW;
+  return (b % BPL) * GW + b / BPL;
+}
+template <int GW>
+__device__ __forceinline__ uint32_t cum_at(const WarpScratch& ws, int b) {
+  return b >= 256 ? 65536u : ws.cum[cum_pos<GW>(b)];
 }
 
 // Per-pixel mixture state held by lane k (< K) for component k.
@@ -384,9 +398,8 @@ __device__ __forceinline__ float channel_table(const CompState& cs, int K, int c
 #pragma unroll
   for (int q = 0; q < BPL; q++) {
     const int qv = __float_as_int(F[q]);
-    ws.cum[b0 + q] = (uint32_t)((qv > excl ? qv : excl) + b0 + q);
+    ws.cum[q * GW + gl] = (uint32_t)((qv > excl ? qv : excl) + b0 + q);
   }
-  if (gl == 0) ws.cum[256] = 65536u;
   __syncwarp();
   return m;
 }
@@ -400,7 +413,7 @@ __device__ __forceinline__ int table_search(const WarpScratch& ws, uint32_t slot
 #pragma unroll
   for (int q = 0; q < BPL; q++) {
     const int b = gl * BPL + q;
-    cnt += (b >= 1 && ws.cum[b] <= slot) ? 1 : 0;
+    cnt += (b >= 1 && ws.cum[q * GW + gl] <= slot) ? 1 : 0;
   }
   return __reduce_add_sync(grp_mask<GW>(lane), cnt);
 }

@@ -444,12 +444,21 @@ static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_v
   tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.wh, C, d.NOp);
   ok &= tc_wait(t);
   const int nh = d.NOp / 2, n0 = half * nh;
-  for (int g = 0; live && g < nh / 8; g++) {
-    float v[8];
-    tmem_ld8(tl + (uint32_t)(n0 + 8 * g), v);
-    float* o = t.P + (size_t)row * d.ldP + n0 + 8 * g;
+  if (live) {
+    // columns n0 .. n0 + nh - 1 in loads of up to 32 columns
+    for (int c = 0; c < nh; c += 32) {
+      const int cw = nh - c < 32 ? nh - c : 32;
+      float v[32];
+      if (cw == 32) {
+        tmem_ld32(tl + (uint32_t)(n0 + c), v);
+      } else {
+        tmem_ld_cols(tl + (uint32_t)(n0 + c), cw & ~7, v);
+      }
+      float* o = t.P + (size_t)row * d.ldP + n0 + c;
 #pragma unroll
-    for (int e = 0; e < 8; e++) o[e] = __fadd_rn(v[e], bh[n0 + 8 * g + e]);
+      for (int e = 0; e < 32; e++)
+        if (e < (cw & ~7)) o[e] = __fadd_rn(v[e], bh[n0 + c + e]);
+    }
   }
   fence_before_sync();
   __syncthreads();

@@ -123,7 +123,7 @@ struct GroupRansDec {
   __device__ __forceinline__ int decode(const WarpScratch& ws, int lane) {
     const uint32_t slot = x & 0xFFFFu;
     const int s = table_search<GW>(ws, slot, lane);
-    const uint32_t c0 = ws.cum[s], c1 = ws.cum[s + 1];
+    const uint32_t c0 = cum_at<GW>(ws, s), c1 = cum_at<GW>(ws, s + 1);
     x = (c1 - c0) * (x >> 16) + slot - c0;
     for (int it = 0; it < 3 && x < kRansL; it++) {
       const uint32_t bt = used < 4 ? (lo >> (8 * used)) & 0xFFu
