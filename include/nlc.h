@@ -133,11 +133,14 @@ int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
 /* Decoder phase profile (per-step latency against the dependency-bound step
  * count of Section 3).  enable != 0 makes the following nlc_decompress calls
  * record, in thread 0 of every CTA, clock64 cycles spent per phase; a
- * non-NULL h_counters (8 uint64) receives the totals accumulated since the
+ * non-NULL h_counters (16 uint64) receives the totals accumulated since the
  * last read, summed over CTAs, and clears them:
  *   [0] front bookkeeping, [1] tile slot assignment, [2] context gather and
  *   local network, [3] per-pixel CDF + rANS coding, [4] grid barrier,
- *   [5] tiles processed, [6] CTAs, [7] decode steps (of CTA 0).
+ *   [5] tiles processed, [6] CTAs, [7] decode steps (of CTA 0);
+ *   within [3], for the pixels coded by warp 0: [8] mixture set-up,
+ *   [9] frequency tables, [10] rANS symbol decode, [11] posterior update,
+ *   [12] pixels; [13..15] zero.
  * Synchronises the device when reading or changing the mode. */
 int nlc_decode_profile(nlc_ctx* ctx, int enable, uint64_t* h_counters);
 

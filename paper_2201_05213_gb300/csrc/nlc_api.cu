@@ -239,16 +239,16 @@ extern "C" int nlc_decode_profile(nlc_ctx* x, int enable, uint64_t* h_counters) 
   if (h_counters) {
     if (x->d_prof) {
       CUDA_TRY(cudaDeviceSynchronize());
-      CUDA_TRY(cudaMemcpy(h_counters, x->d_prof, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-      CUDA_TRY(cudaMemset(x->d_prof, 0, 8 * sizeof(uint64_t)));
+      CUDA_TRY(cudaMemcpy(h_counters, x->d_prof, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemset(x->d_prof, 0, 16 * sizeof(uint64_t)));
     } else {
-      memset(h_counters, 0, 8 * sizeof(uint64_t));
+      memset(h_counters, 0, 16 * sizeof(uint64_t));
     }
   }
   if (enable && !x->d_prof) {
     CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMalloc((void**)&x->d_prof, 8 * sizeof(uint64_t)));
-    CUDA_TRY(cudaMemset(x->d_prof, 0, 8 * sizeof(uint64_t)));
+    CUDA_TRY(cudaMalloc((void**)&x->d_prof, 16 * sizeof(uint64_t)));
+    CUDA_TRY(cudaMemset(x->d_prof, 0, 16 * sizeof(uint64_t)));
   } else if (!enable && x->d_prof) {
     CUDA_TRY(cudaDeviceSynchronize());
     cudaFree(x->d_prof);

@@ -43,6 +43,9 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / GW, gl = lane % GW;
   const int K = a.m.d.K, ldP = a.m.d.ldP;
+  // sub-stage cycles of thread 0: mixture set-up, tables, rANS, posterior
+  const bool prof = a.prof != nullptr && threadIdx.x == 0;
+  long long s_init = 0, s_tab = 0, s_dec = 0, s_obs = 0, s_px = 0, c0 = 0, c1 = 0;
   for (int j = 0; gpw * warp + kWarps * gpw * j < n; j++) {
     const int s = gpw * warp + grp + kWarps * gpw * j;
     const bool valid = s < n;
@@ -61,13 +64,18 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
     const int sid = ps.aux;
     WarpScratch& ws = t.ws[gpw * warp + grp];
     CompState cs;
+    if (prof) c0 = clock64();
     comp_init<GW>(t.U0 + (size_t)se * ldP, K, gl, cs);
+    if (prof) { c1 = clock64(); s_init += c1 - c0; c0 = c1; s_px++; }
     int v[3] = {0, 0, 0};
     for (int ch = 0; ch < 3; ch++) {
       const float mloc = channel_table<GW>(cs, K, ch, v[0], v[1], gl, ws);
+      if (prof) { c1 = clock64(); s_tab += c1 - c0; c0 = c1; }
       v[ch] = dec.decode<GW>(ws, lane);
+      if (prof) { c1 = clock64(); s_dec += c1 - c0; c0 = c1; }
       if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
       __syncwarp();
+      if (prof) { c1 = clock64(); s_obs += c1 - c0; c0 = c1; }
     }
     if (gl == 0 && valid) {
       uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
@@ -80,6 +88,13 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       const bool last = a.layout == 1 ? (ps.j == U.Wu - 1) : (ps.i == U.Hu - 1 && ps.j == U.Wu - 1);
       if (dec.bad || (last && (dec.x != kRansL || np != dec.end))) set_status(a.status, ST_CORRUPT);
     }
+  }
+  if (prof) {
+    atomicAdd(a.prof + 8, (unsigned long long)s_init);
+    atomicAdd(a.prof + 9, (unsigned long long)s_tab);
+    atomicAdd(a.prof + 10, (unsigned long long)s_dec);
+    atomicAdd(a.prof + 11, (unsigned long long)s_obs);
+    atomicAdd(a.prof + 12, (unsigned long long)s_px);
   }
 }
 

@@ -251,8 +251,13 @@ __device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
 // cum holds cum_0 .. cum_255 lane-interleaved (see cum_pos); cum_256 = 2^16.
 struct alignas(16) WarpScratch {
   float al[kMaxK], be[kMaxK], w[kMaxK], rr[kMaxK];
+  int act[kMaxK];  // components with weight >= kWmin, in increasing order
   uint32_t cum[256];
 };
+
+// Components whose weight is below 2^-17 are left out of the CDF: together
+// they move 65280 F(b) by at most half a count per component.
+constexpr float kWmin = 7.62939453125e-06f;
 static_assert(sizeof(WarpScratch) % 16 == 0, "WarpScratch keeps 16-byte alignment in arrays");
 
 // ---------------------------------------------------------------------
@@ -344,6 +349,7 @@ __device__ __forceinline__ float channel_table(const CompState& cs, int K, int c
   const float mx = grp_max<GW>(lw);
   const float e = gl < K ? exp_f(__fsub_rn(lw, mx)) : 0.f;
   const float s = grp_sum<GW>(e);
+  float wk_own = 0.f;
   if (gl < K) {
     m = comp_mean(cs, ch, r, g);
     const float c = __fmul_rn(exp_f(-cs.ls[ch]), kLog2e);
@@ -351,8 +357,17 @@ __device__ __forceinline__ float channel_table(const CompState& cs, int K, int c
     ws.al[gl] = al;
     ws.be[gl] = __fmul_rn(c, __fadd_rn(m, 256.f * kInv255));
     ws.rr[gl] = ex2_approx(-al);
-    ws.w[gl] = __fdiv_rn(e, s);
+    wk_own = __fdiv_rn(e, s);
+    ws.w[gl] = wk_own;
   }
+  // the group's active components, compacted in increasing order; the
+  // weights sum to one, so at least one is active
+  const bool on_own = gl < K && wk_own >= kWmin;
+  const unsigned bal = __ballot_sync(0xffffffffu, on_own);
+  const unsigned gbits = GW == 32 ? bal : ((bal >> (threadIdx.x & 16)) & 0xFFFFu);
+  if (on_own) ws.act[__popc(gbits & ((1u << gl) - 1u))] = gl;
+  const int nact = __popc(gbits);
+  const int nmax = GW == 32 ? nact : max(nact, __shfl_xor_sync(0xffffffffu, nact, 16));
   __syncwarp();
   float F[BPL];
 #pragma unroll
@@ -362,8 +377,13 @@ __device__ __forceinline__ float channel_table(const CompState& cs, int K, int c
   // Chains of 8 boundaries restart from an exact ex2: with |y| clamped at
   // 126 and al <= 12.4 (log-scale >= -7), seven steps from a clamped start
   // stay beyond |y| = 39, where the logistic is 0 or 1 to within 2^-39.
-  for (int k = 0; k < K; k++) {
-    const float al = ws.al[k], rk = ws.rr[k], wk = ws.w[k], be = ws.be[k];
+  // A group whose list is shorter than its neighbour's repeats its first
+  // component with weight 0, which leaves F unchanged (F >= 0, finite).
+  for (int i = 0; i < nmax; i++) {
+    const bool live = i < nact;
+    const int k = ws.act[live ? i : 0];
+    const float al = ws.al[k], rk = ws.rr[k], be = ws.be[k];
+    const float wk = live ? ws.w[k] : 0.f;
     float E = 0.f;
 #pragma unroll
     for (int q = 0; q < BPL; q++) {

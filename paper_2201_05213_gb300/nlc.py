@@ -177,8 +177,8 @@ def nlc_sync_status(ctx, stream=None):
 
 
 def nlc_decode_profile(ctx, enable, read=True):
-    """Enables/disables decoder phase profiling; returns the 8 counters (or None)."""
-    out = np.zeros(8, dtype=np.uint64) if read else None
+    """Enables/disables decoder phase profiling; returns the 16 counters (or None)."""
+    out = np.zeros(16, dtype=np.uint64) if read else None
     _check(load().nlc_decode_profile(ctx, int(enable), _ptr(out) if read else None))
     return out
 
