@@ -301,7 +301,7 @@ def main():
                 for i, name in enumerate(["front", "slots", "gather_network", "coding", "barrier"])}
     npx0 = max(float(cnt[12]), 1.0)
     coding_us = {name: float(cnt[8 + i]) / npx0 / mhz
-                 for i, name in enumerate(["mixture_setup", "tables", "rans", "posterior"])}
+                 for i, name in enumerate(["setup", "cdf_search", "rans", "posterior"])}
     phases = {"steps": steps_T, "ctas": ctas, "tiles_per_cta_step": float(cnt[5]) / ctas / steps_T,
               "us_per_step_measured": 1000.0 * ms / steps_T,
               "us_per_step_by_phase_at_2070MHz": phase_us,

@@ -109,7 +109,11 @@ int nlc_abi_version(void);
 size_t nlc_num_weights(const nlc_model_cfg* cfg);
 
 /* Creates a context on the current device with the given host weights
- * (n_weights must equal nlc_num_weights(cfg)).  Synchronous. */
+ * (n_weights must equal nlc_num_weights(cfg)).  Synchronous.  The first call
+ * on a device also checks, over every pair of adjacent floats in the ranges
+ * used, that the device's ex2.approx and rcp.approx are monotone (about a
+ * millisecond); the frequency tables are computed one boundary at a time and
+ * rely on it.  If the check fails: NLC_ERR_UNSUPPORTED. */
 int nlc_create(const nlc_model_cfg* cfg, const float* h_weights, size_t n_weights, nlc_ctx** out);
 int nlc_destroy(nlc_ctx* ctx);
 
@@ -138,9 +142,9 @@ int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
  *   [0] front bookkeeping, [1] tile slot assignment, [2] context gather and
  *   local network, [3] per-pixel CDF + rANS coding, [4] grid barrier,
  *   [5] tiles processed, [6] CTAs, [7] decode steps (of CTA 0);
- *   within [3], for the pixels coded by warp 0: [8] mixture set-up,
- *   [9] frequency tables, [10] rANS symbol decode, [11] posterior update,
- *   [12] pixels; [13..15] zero.
+ *   within [3], for the pixels coded by warp 0: [8] mixture and channel
+ *   set-up, [9] CDF symbol search, [10] rANS state update, [11] posterior
+ *   update, [12] pixels; [13..15] zero.
  * Synchronises the device when reading or changing the mode. */
 int nlc_decode_profile(nlc_ctx* ctx, int enable, uint64_t* h_counters);
 

@@ -129,6 +129,28 @@ extern "C" int nlc_destroy(nlc_ctx* x) {
   return NLC_OK;
 }
 
+// Result of the monotonicity check of the MUFU approximations per device
+// (0 = not run, 1 = passed, -1 = failed), run once per device and process.
+static std::mutex g_mono_mu;
+static int g_mono[64];
+
+static int check_mono(int device, int sm_count, unsigned long long* d_scratch) {
+  std::lock_guard<std::mutex> lock(g_mono_mu);
+  const int slot = device >= 0 && device < 64 ? device : 63;
+  if (g_mono[slot] == 0) {
+    cudaError_t e = launch_mono_check(d_scratch, sm_count, 0);
+    unsigned long long viol = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&viol, d_scratch, 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(NLC_ERR_CUDA, "device check failed: %s", cudaGetErrorString(e));
+    g_mono[slot] = viol == 0 ? 1 : -1;
+  }
+  if (g_mono[slot] < 0)
+    return fail(NLC_ERR_UNSUPPORTED,
+                "ex2.approx / rcp.approx are not monotone on this device; the frequency tables "
+                "need them to be");
+  return NLC_OK;
+}
+
 extern "C" int nlc_create(const nlc_model_cfg* cfg, const float* h_w, size_t n, nlc_ctx** out) {
   if (!out) return fail(NLC_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -165,6 +187,8 @@ extern "C" int nlc_create(const nlc_model_cfg* cfg, const float* h_w, size_t n, 
     TRY_ALLOC(x->d_v, n * 4);
     TRY_ALLOC(x->d_grad, n * 4);
     TRY_ALLOC(x->d_loss, 8);
+    rc = check_mono(x->device, x->sm_count, reinterpret_cast<unsigned long long*>(x->d_loss));
+    if (rc) break;
     if ((e = cudaMemcpy(x->d_w, h_w, n * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(x->d_status, 0, 4)) != cudaSuccess ||
         (e = cudaMemset(x->d_m, 0, n * 4)) != cudaSuccess ||

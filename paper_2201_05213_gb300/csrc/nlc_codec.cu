@@ -485,7 +485,8 @@ cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t
 __global__ void tables_kernel(int K, int NO, const float* __restrict__ params,
                               const uint8_t* __restrict__ pixels, long long n,
                               uint32_t* __restrict__ cum) {
-  // the codec's 16-lane coding groups, two pixels per warp
+  // the codec's 16-lane coding groups, two pixels per warp; lanes take the
+  // boundaries gl, gl + 16, ... with all active components each
   __shared__ WarpScratch ws[kGroups];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = lane >> 4, gl = lane & (kGW - 1);
@@ -499,10 +500,13 @@ __global__ void tables_kernel(int K, int NO, const float* __restrict__ params,
     CompState cs;
     comp_init<kGW>(params + qe * NO, K, gl, cs);
     for (int ch = 0; ch < 3; ch++) {
-      const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, g);
+      int nact;
+      const float mloc = channel_setup<kGW>(cs, K, ch, v[0], v[1], gl, g, nact);
       uint32_t* o = cum + (qe * 3 + ch) * 257;
-      if (valid)
-        for (int b = gl; b < 257; b += kGW) o[b] = cum_at<kGW>(g, b);
+      for (int b = gl; b < 257; b += kGW) {
+        const uint32_t u = cum_fix(b >= 1 && b <= 255 ? cdf_fix(g, nact, edge_f(b), 0, 1) : 0, b);
+        if (valid) o[b] = u;
+      }
       if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
       __syncwarp();
     }
@@ -545,7 +549,7 @@ __global__ void rans_dec_test_kernel(const uint8_t* __restrict__ in, long long s
                                      const uint32_t* __restrict__ cum,
                                      const long long* __restrict__ sym_off, int n_streams,
                                      int32_t* __restrict__ sym, int* status) {
-  __shared__ WarpScratch ws[kWarps];
+  __shared__ TableScratch ws[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = blockIdx.x * kWarps + warp;
   if (s >= n_streams) return;
@@ -565,7 +569,7 @@ __global__ void rans_dec_test_kernel(const uint8_t* __restrict__ in, long long s
     for (int b = lane; b < 256; b += 32) ws[warp].cum[cum_pos<32>(b)] = cum[k * 257 + b];
     __syncwarp();
     dec.load_bytes(base);
-    const int v = dec.decode<32>(ws[warp], lane);
+    const int v = dec.decode_table<32>(ws[warp], lane);
     dec.pos += dec.used;
     if (lane == 0) sym[k] = v;
     __syncwarp();
@@ -579,6 +583,48 @@ cudaError_t launch_rans_decode(const uint8_t* in, long long stride, const int32_
   if (n_streams == 0) return cudaSuccess;
   rans_dec_test_kernel<<<grid_for(n_streams, kWarps, 1 << 20), kThreads, 0, s>>>(
       in, stride, lens, cum, sym_off, n_streams, sym, status);
+  return cudaGetLastError();
+}
+
+}  // namespace nlc
+
+namespace nlc {
+
+// ---------------------------------------------------------------------
+// Device check behind the pointwise CDF: ex2.approx must be non-decreasing
+// on [-126, 126] and rcp.approx non-increasing on [1, 2^127).  Every pair of
+// adjacent floats in those ranges is compared (3.3e9 pairs, about a
+// millisecond); viol receives the number of pairs out of order.
+// ---------------------------------------------------------------------
+__global__ void mono_check_kernel(unsigned long long* viol) {
+  constexpr uint32_t kB126 = 0x42FC0000u;  // bit pattern of 126.0f
+  constexpr uint32_t kOne = 0x3F800000u, kTop = 0x7F000000u;
+  // ranges of bit patterns b, each compared with b + 1:
+  //   [0, kB126): x = +0 .. 126, ex2 non-decreasing
+  //   [kB126, 2 kB126): x = -0 .. -126 (value falls as bits rise), ex2 non-increasing
+  //   [2 kB126, 2 kB126 + kTop - kOne): x = 1 .. 2^127, rcp non-increasing
+  const unsigned long long n = 2ull * kB126 + (kTop - kOne);
+  unsigned long long bad = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (i < kB126) {
+      const uint32_t b = (uint32_t)i;
+      bad += ex2_approx(__uint_as_float(b + 1)) < ex2_approx(__uint_as_float(b)) ? 1 : 0;
+    } else if (i < 2ull * kB126) {
+      const uint32_t b = 0x80000000u | (uint32_t)(i - kB126);
+      bad += ex2_approx(__uint_as_float(b + 1)) > ex2_approx(__uint_as_float(b)) ? 1 : 0;
+    } else {
+      const uint32_t b = kOne + (uint32_t)(i - 2ull * kB126);
+      bad += rcp_approx(__uint_as_float(b + 1)) > rcp_approx(__uint_as_float(b)) ? 1 : 0;
+    }
+  }
+  if (bad) atomicAdd(viol, bad);
+}
+
+cudaError_t launch_mono_check(unsigned long long* viol, int sm_count, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(viol, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  mono_check_kernel<<<sm_count * 8, 256, 0, s>>>(viol);
   return cudaGetLastError();
 }
 

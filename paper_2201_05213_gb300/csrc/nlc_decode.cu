@@ -69,9 +69,14 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
     if (prof) { c1 = clock64(); s_init += c1 - c0; c0 = c1; s_px++; }
     int v[3] = {0, 0, 0};
     for (int ch = 0; ch < 3; ch++) {
-      const float mloc = channel_table<GW>(cs, K, ch, v[0], v[1], gl, ws);
+      int nact;
+      const float mloc = channel_setup<GW>(cs, K, ch, v[0], v[1], gl, ws, nact);
+      if (prof) { c1 = clock64(); s_init += c1 - c0; c0 = c1; }
+      const uint32_t slot = dec.x & 0xFFFFu;
+      uint32_t lo, hi;
+      v[ch] = cdf_search<GW>(ws, nact, slot, gl, lo, hi);
       if (prof) { c1 = clock64(); s_tab += c1 - c0; c0 = c1; }
-      v[ch] = dec.decode<GW>(ws, lane);
+      dec.advance(slot, lo, hi);
       if (prof) { c1 = clock64(); s_dec += c1 - c0; c0 = c1; }
       if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
       __syncwarp();

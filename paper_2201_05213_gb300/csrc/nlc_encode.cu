@@ -53,8 +53,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       CompState cs;
       comp_init<kGW>(t.U0 + (size_t)se * ldP, K, gl, cs);
       for (int ch = 0; ch < 3; ch++) {
-        const float mloc = channel_table<kGW>(cs, K, ch, v[0], v[1], gl, ws);
-        const uint32_t c0 = cum_at<kGW>(ws, v[ch]), c1 = cum_at<kGW>(ws, v[ch] + 1);
+        int nact;
+        const float mloc = channel_setup<kGW>(cs, K, ch, v[0], v[1], gl, ws, nact);
+        uint32_t c0, c1;
+        cdf_pair<kGW>(ws, v[ch], gl, c0, c1);
         if (gl == 0 && valid) stage[3 * q + ch] = c0 | ((c1 - c0) << 16);
         if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
         __syncwarp();

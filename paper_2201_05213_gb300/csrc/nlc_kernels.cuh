@@ -77,5 +77,8 @@ cudaError_t launch_rans_encode(const uint32_t* start, const uint32_t* freq,
 cudaError_t launch_rans_decode(const uint8_t* in, long long stride, const int32_t* lens,
                                const uint32_t* cum, const long long* sym_off, int n_streams,
                                int32_t* sym, int* status, cudaStream_t s);
+// Counts adjacent float pairs on which ex2.approx / rcp.approx are not
+// monotone over the ranges the frequency tables use (0 expected).
+cudaError_t launch_mono_check(unsigned long long* viol, int sm_count, cudaStream_t s);
 
 }  // namespace nlc

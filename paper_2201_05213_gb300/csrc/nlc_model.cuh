@@ -206,6 +206,8 @@ __device__ void network_simt_run(const Dims& d, const float* Wt, float* A, float
 //   cum_b = Q_b + b, cum_256 = 2^16,
 // so every frequency is >= 1 and they sum to 2^16.  Component weights:
 // R: pi_k; G: prop. to pi_k P_Rk(r); B: prop. to pi_k P_Rk(r) P_Gk(g).
+// The device evaluates F so that it is non-decreasing in b (cdf_term
+// below); then Q_b = q_b and any cum_b is computed on its own.
 // ---------------------------------------------------------------------
 constexpr float kInv255 = 1.f / 255.f;
 constexpr float kLog2e = 1.4426950408889634f;
@@ -247,26 +249,32 @@ __device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
   return __fadd_rn(__fsub_rn(-softplus_f(-a), softplus_f(b)), lme);
 }
 
-// Scratch of one coding group (a warp, or half a warp) in the CDF stage.
-// cum holds cum_0 .. cum_255 lane-interleaved (see cum_pos); cum_256 = 2^16.
+// Scratch of one coding group (a warp, or half a warp) in the CDF stage:
+// the channel's active components (weight >= kWmin), compacted in
+// increasing component order, as (m_k, c_k = log2(e)/s_k, w_k 2^23, 0),
+// then zero entries (weight 0, term 0) up to 2 kMaxK, so that unrolled
+// loops may read past the last active component.
 struct alignas(16) WarpScratch {
-  float al[kMaxK], be[kMaxK], w[kMaxK], rr[kMaxK];
-  int act[kMaxK];  // components with weight >= kWmin, in increasing order
+  float4 cp[2 * kMaxK];
+};
+
+// Table of one coding warp for decoding with an explicit cum[0..255]
+// (lane-interleaved, see cum_pos); cum_256 = 2^16.
+struct TableScratch {
   uint32_t cum[256];
 };
 
 // Components whose weight is below 2^-17 are left out of the CDF: together
 // they move 65280 F(b) by at most half a count per component.
 constexpr float kWmin = 7.62939453125e-06f;
-static_assert(sizeof(WarpScratch) % 16 == 0, "WarpScratch keeps 16-byte alignment in arrays");
 
 // ---------------------------------------------------------------------
-// Coding groups.  One pixel's channel tables are built by a group of GW
-// lanes (GW = 32: a whole warp; GW = 16: half a warp, so that a warp codes
-// two pixels at once).  Lane gl of a group owns the BPL = 256/GW boundaries
-// b = BPL gl .. BPL gl + BPL - 1; lanes gl < K also hold component gl.  All
-// group reductions are xor butterflies, which give the same value in every
-// lane of the group.  The encoder and the decoder use the same GW.
+// Coding groups.  One pixel's channels are coded by a group of GW lanes
+// (GW = 32: a whole warp; GW = 16: half a warp, so that a warp codes two
+// pixels at once); lanes gl < K of a group hold component gl.  Group
+// reductions over floats are xor butterflies, which give the same value in
+// every lane of the group and, for K <= 16, the same value for GW = 16 and
+// GW = 32 (the upper half adds exact zeros first).
 // ---------------------------------------------------------------------
 template <int GW>
 __device__ __forceinline__ float grp_max(float v) {
@@ -284,8 +292,14 @@ template <int GW>
 __device__ __forceinline__ unsigned grp_mask(int lane) {
   return GW == 32 ? 0xffffffffu : (0xFFFFu << (lane & 16));
 }
+// The group's bits of a warp ballot, group lane 0 in bit 0.
+template <int GW>
+__device__ __forceinline__ unsigned grp_ballot(bool p) {
+  const unsigned b = __ballot_sync(0xffffffffu, p);
+  return GW == 32 ? b : ((b >> (threadIdx.x & 16)) & 0xFFFFu);
+}
 
-// Position of cum_b (b < 256) in WarpScratch::cum for groups of GW lanes:
+// Position of cum_b (b < 256) in TableScratch::cum for groups of GW lanes:
 // lane gl's boundaries b = BPL gl + q sit at q GW + gl, so the group's
 // stores and loads of one q hit consecutive banks.
 template <int GW>
@@ -294,7 +308,7 @@ __device__ __forceinline__ int cum_pos(int b) {
   return (b % BPL) * GW + b / BPL;
 }
 template <int GW>
-__device__ __forceinline__ uint32_t cum_at(const WarpScratch& ws, int b) {
+__device__ __forceinline__ uint32_t cum_at(const TableScratch& ws, int b) {
   return b >= 256 ? 65536u : ws.cum[cum_pos<GW>(b)];
 }
 
@@ -302,6 +316,7 @@ __device__ __forceinline__ uint32_t cum_at(const WarpScratch& ws, int b) {
 struct CompState {
   float logpi, lw;      // log pi_k, running log weight
   float mu[3], ls[3], co[3];
+  float c[3];           // log2(e) / s_{c,k}
 };
 
 template <int GW = 32>
@@ -319,6 +334,7 @@ __device__ __forceinline__ void comp_init(const float* P, int K, int gl, CompSta
       cs.mu[c] = P[K + c * K + gl];
       cs.ls[c] = fmaxf(P[4 * K + c * K + gl], -7.f);
       cs.co[c] = tanhf(P[7 * K + c * K + gl]);
+      cs.c[c] = __fmul_rn(exp_f(-cs.ls[c]), kLog2e);
     }
   }
 }
@@ -331,102 +347,140 @@ __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, i
   return __fadd_rn(__fadd_rn(cs.mu[2], __fmul_rn(cs.co[1], xr)), __fmul_rn(cs.co[2], xg));
 }
 
-// Builds cum[0..256] of channel ch in ws.cum (whole group).  Returns the
-// location of the lane's component (for the posterior update).
-//
-// With y_k(b) = -(e_b - m_k)/s_k log2(e) = be_k - b al_k, component k's
-// logistic is 1/(1 + 2^y): one ex2 at the lane's first boundary, then 2^y of
-// the next boundary by one multiply with 2^-al_k, and one rcp per boundary.
-// The sum runs over k in a fixed order, so F(b) is the same expression of the
-// pixel's parameters in every kernel that uses the same GW.
+// ---------------------------------------------------------------------
+// Pointwise quantised CDF.  F(b) is a fixed-point number in units of 2^-23:
+// the sum over the active components of rint(w_k 2^23 sigmoid((e_b-m_k)/s_k)).
+// Every operation from b to a term is non-decreasing in b: correctly
+// rounded arithmetic with fixed operands, clamps, rint, and the MUFU
+// approximations ex2.approx (on [-126, 126]) and rcp.approx (on [1, 2^127)),
+// which are monotone on sm_103 (checked exhaustively over those ranges by
+// the library before a context is created, see mono_check_kernel).  So F is
+// non-decreasing in b as computed, the running max of the quantiser leaves q
+// unchanged, and each cum_b follows from b alone.  Integer sums do not
+// depend on the order of their terms: every split of the components over
+// lanes, in the encoder, the decoder or the table entry point, gives the
+// same cum_b.
+// ---------------------------------------------------------------------
+constexpr float kFixOne = 8388608.f;           // 2^23
+constexpr uint32_t kFixOneBits = 0x4B000000u;  // bit pattern of 2^23
+constexpr float kZMax = 126.f;                 // |z| clamp of the logistic's 2^z
+
+// One component's term of F at boundary value e: the logistic is
+// 1/(1 + 2^z) with z = (m - e) log2(e)/s clamped to [-126, 126], and
+// x = w 2^23 sigmoid lies in [0, 2^23]; x + 2^23 rounded to nearest is
+// 2^23 + rint(x) (float spacing 1 in [2^23, 2^24]), read back from its bits.
+__device__ __forceinline__ uint32_t cdf_term(float e, const float4& p) {
+  const float z = fminf(fmaxf(__fmul_rn(__fsub_rn(p.x, e), p.y), -kZMax), kZMax);
+  const float x = __fmul_rn(p.z, rcp_approx(__fadd_rn(1.f, ex2_approx(z))));
+  return (uint32_t)__float_as_int(__fadd_rn(x, kFixOne)) - kFixOneBits;
+}
+
+// Partial fixed-point F at boundary value e over components i0, i0 + di, ...
+// (di <= 4), four independent terms at a time; entries past the active ones
+// are zero.
+__device__ __forceinline__ uint32_t cdf_fix(const WarpScratch& ws, int nact, float e, int i0,
+                                            int di) {
+  uint32_t F = 0;
+  for (int i = i0; i < nact; i += 4 * di) {
+    const uint32_t t0 = cdf_term(e, ws.cp[i]);
+    const uint32_t t1 = cdf_term(e, ws.cp[i + di]);
+    const uint32_t t2 = cdf_term(e, ws.cp[i + 2 * di]);
+    const uint32_t t3 = cdf_term(e, ws.cp[i + 3 * di]);
+    F += (t0 + t1) + (t2 + t3);
+  }
+  return F;
+}
+
+// cum_b = q_b + b with q_b = clamp(rint(65280 F), 0, 65280), F = Fi 2^-23
+// (ties to even); cum_0 = 0 and cum_256 = 2^16.
+__device__ __forceinline__ uint32_t cum_fix(uint32_t Fi, int b) {
+  if (b <= 0) return 0u;
+  if (b >= 256) return 65536u;
+  const unsigned long long P = (unsigned long long)Fi * (unsigned long long)kMq;
+  uint32_t q = (uint32_t)(P >> 23);
+  const uint32_t r = (uint32_t)(P & 0x7FFFFFull);
+  q += (r > 0x400000u || (r == 0x400000u && (q & 1u))) ? 1u : 0u;
+  return (q < (uint32_t)kMq ? q : (uint32_t)kMq) + (uint32_t)b;
+}
+
+// Channel ch of the pixel: component weights (softmax of the running log
+// weights) and locations, compacted into ws.cp.  Returns the location of the
+// lane's component (for the posterior update); nact = active components.
 template <int GW>
-__device__ __forceinline__ float channel_table(const CompState& cs, int K, int ch, int r, int g,
-                                               int gl, WarpScratch& ws) {
-  constexpr int BPL = 256 / GW;
-  float m = 0.f;
-  // component weights: softmax of the running log weights
+__device__ __forceinline__ float channel_setup(const CompState& cs, int K, int ch, int r, int g,
+                                               int gl, WarpScratch& ws, int& nact) {
   const float lw = gl < K ? cs.lw : -INFINITY;
   const float mx = grp_max<GW>(lw);
   const float e = gl < K ? exp_f(__fsub_rn(lw, mx)) : 0.f;
   const float s = grp_sum<GW>(e);
-  float wk_own = 0.f;
+  float m = 0.f, wk = 0.f;
   if (gl < K) {
     m = comp_mean(cs, ch, r, g);
-    const float c = __fmul_rn(exp_f(-cs.ls[ch]), kLog2e);
-    const float al = __fmul_rn(c, 2.f * kInv255);
-    ws.al[gl] = al;
-    ws.be[gl] = __fmul_rn(c, __fadd_rn(m, 256.f * kInv255));
-    ws.rr[gl] = ex2_approx(-al);
-    wk_own = __fdiv_rn(e, s);
-    ws.w[gl] = wk_own;
+    wk = __fdiv_rn(e, s);
   }
-  // the group's active components, compacted in increasing order; the
-  // weights sum to one, so at least one is active
-  const bool on_own = gl < K && wk_own >= kWmin;
-  const unsigned bal = __ballot_sync(0xffffffffu, on_own);
-  const unsigned gbits = GW == 32 ? bal : ((bal >> (threadIdx.x & 16)) & 0xFFFFu);
-  if (on_own) ws.act[__popc(gbits & ((1u << gl) - 1u))] = gl;
-  const int nact = __popc(gbits);
-  const int nmax = GW == 32 ? nact : max(nact, __shfl_xor_sync(0xffffffffu, nact, 16));
-  __syncwarp();
-  float F[BPL];
-#pragma unroll
-  for (int q = 0; q < BPL; q++) F[q] = 0.f;
-  const int b0 = gl * BPL;
-  const float fb0 = (float)b0;
-  // Chains of 8 boundaries restart from an exact ex2: with |y| clamped at
-  // 126 and al <= 12.4 (log-scale >= -7), seven steps from a clamped start
-  // stay beyond |y| = 39, where the logistic is 0 or 1 to within 2^-39.
-  // A group whose list is shorter than its neighbour's repeats its first
-  // component with weight 0, which leaves F unchanged (F >= 0, finite).
-  for (int i = 0; i < nmax; i++) {
-    const bool live = i < nact;
-    const int k = ws.act[live ? i : 0];
-    const float al = ws.al[k], rk = ws.rr[k], be = ws.be[k];
-    const float wk = live ? ws.w[k] : 0.f;
-    float E = 0.f;
-#pragma unroll
-    for (int q = 0; q < BPL; q++) {
-      if ((q & 7) == 0) {
-        float y = __fmaf_rn(-(fb0 + (float)q), al, be);
-        y = fminf(fmaxf(y, -126.f), 126.f);
-        E = ex2_approx(y);
-      } else {
-        E = __fmul_rn(E, rk);
-      }
-      F[q] = __fmaf_rn(wk, rcp_approx(__fadd_rn(1.f, E)), F[q]);
-    }
-  }
-  // quantise, running max within the lane, then across the group
-  int Q = 0;
-#pragma unroll
-  for (int q = 0; q < BPL; q++) {
-    int v = __float2int_rn(__fmul_rn(65280.f, F[q]));
-    v = v < 0 ? 0 : (v > kMq ? kMq : v);
-    if (b0 + q == 0) v = 0;
-    Q = v > Q ? v : Q;
-    F[q] = __int_as_float(Q);  // reuse the registers for the running max
-  }
-  int pre = Q;  // inclusive max over group lanes <= gl
-#pragma unroll
-  for (int o = 1; o < GW; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, pre, o, GW);
-    if (gl >= o) pre = t > pre ? t : pre;
-  }
-  int excl = __shfl_up_sync(0xffffffffu, pre, 1, GW);
-  if (gl == 0) excl = 0;
-#pragma unroll
-  for (int q = 0; q < BPL; q++) {
-    const int qv = __float_as_int(F[q]);
-    ws.cum[q * GW + gl] = (uint32_t)((qv > excl ? qv : excl) + b0 + q);
-  }
+  // the weights sum to one, so at least one component is active
+  const bool on = gl < K && wk >= kWmin;
+  const unsigned bits = grp_ballot<GW>(on);
+  nact = __popc(bits);
+  for (int p = gl; p < 2 * kMaxK; p += GW)
+    if (p >= nact) ws.cp[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (on) ws.cp[__popc(bits & ((1u << gl) - 1u))] = make_float4(m, cs.c[ch], __fmul_rn(wk, kFixOne), 0.f);
   __syncwarp();
   return m;
 }
 
-// Symbol s with cum_s <= slot < cum_{s+1} (cum strictly increasing).
+// Decoder's symbol search for slot in [0, 2^16): s with cum_s <= slot <
+// cum_{s+1}, and those two values.  Round 1: lane gl evaluates cum at
+// b = B (gl + 1) (B = 256/GW; the last lane holds cum_256); the count c of
+// those <= slot locates s in [B c, B c + B).  Round 2: the B - 1 boundaries
+// inside, with the components split over the GW/B lanes that share one.
 template <int GW>
-__device__ __forceinline__ int table_search(const WarpScratch& ws, uint32_t slot, int lane) {
+__device__ __forceinline__ int cdf_search(const WarpScratch& ws, int nact, uint32_t slot, int gl,
+                                          uint32_t& c0, uint32_t& c1) {
+  constexpr int B = 256 / GW;
+  constexpr int P = GW / B;
+  const unsigned full = 0xffffffffu;
+  uint32_t u1 = 65536u;
+  if (gl < GW - 1) {
+    const int b = B * (gl + 1);
+    u1 = cum_fix(cdf_fix(ws, nact, edge_f(b), 0, 1), b);
+  }
+  const int c = __popc(grp_ballot<GW>(u1 <= slot));
+  const int j = gl % B, part = gl / B;
+  const int b2 = B * c + j + 1;
+  uint32_t F2 = 0;
+  if (j < B - 1) F2 = cdf_fix(ws, nact, edge_f(b2), part, P);
+#pragma unroll
+  for (int o = B; o < GW; o <<= 1) F2 += __shfl_xor_sync(full, F2, o, GW);
+  const uint32_t top = __shfl_sync(full, u1, c, GW);  // cum_{B (c+1)}
+  const uint32_t u2 = j < B - 1 ? cum_fix(F2, b2) : top;
+  const int c2 = __popc(grp_ballot<GW>(part == 0 && u2 <= slot));
+  c1 = __shfl_sync(full, u2, c2, GW);
+  const uint32_t lo2 = __shfl_sync(full, u2, c2 > 0 ? c2 - 1 : 0, GW);
+  const uint32_t lo1 = __shfl_sync(full, u1, c > 0 ? c - 1 : 0, GW);
+  c0 = c2 > 0 ? lo2 : (c > 0 ? lo1 : 0u);
+  return B * c + c2;
+}
+
+// Encoder's pair cum_v, cum_{v+1}: lanes of even / odd gl evaluate b = v /
+// v + 1 over components gl/2 and gl/2 + GW/2 (K <= 16: every component once).
+template <int GW>
+__device__ __forceinline__ void cdf_pair(const WarpScratch& ws, int v, int gl, uint32_t& c0,
+                                         uint32_t& c1) {
+  const unsigned full = 0xffffffffu;
+  const int b = v + (gl & 1);
+  const float e = edge_f(b);
+  uint32_t F = cdf_term(e, ws.cp[gl >> 1]) + cdf_term(e, ws.cp[(gl >> 1) + GW / 2]);
+#pragma unroll
+  for (int o = 2; o < GW; o <<= 1) F += __shfl_xor_sync(full, F, o, GW);
+  const uint32_t u = cum_fix(F, b);
+  c0 = __shfl_sync(full, u, 0, GW);
+  c1 = __shfl_sync(full, u, 1, GW);
+}
+
+// Symbol s with cum_s <= slot < cum_{s+1} in an explicit table.
+template <int GW>
+__device__ __forceinline__ int table_search(const TableScratch& ws, uint32_t slot, int lane) {
   constexpr int BPL = 256 / GW;
   const int gl = lane & (GW - 1);
   int cnt = 0;

@@ -117,13 +117,9 @@ struct GroupRansDec {
     }
     used = 0;
   }
-  // slot = x mod 2^16, symbol s with cum_s <= slot < cum_{s+1},
+  // With slot = x mod 2^16 and the decoded symbol's cum_s <= slot < cum_{s+1}:
   // x = freq (x >> 16) + slot - cum_s, then shift bytes in while x < 2^23.
-  template <int GW>
-  __device__ __forceinline__ int decode(const WarpScratch& ws, int lane) {
-    const uint32_t slot = x & 0xFFFFu;
-    const int s = table_search<GW>(ws, slot, lane);
-    const uint32_t c0 = cum_at<GW>(ws, s), c1 = cum_at<GW>(ws, s + 1);
+  __device__ __forceinline__ void advance(uint32_t slot, uint32_t c0, uint32_t c1) {
     x = (c1 - c0) * (x >> 16) + slot - c0;
     for (int it = 0; it < 3 && x < kRansL; it++) {
       const uint32_t bt = used < 4 ? (lo >> (8 * used)) & 0xFFu
@@ -133,6 +129,13 @@ struct GroupRansDec {
       used++;
     }
     if (x < kRansL) bad = true;
+  }
+  // One symbol from an explicit table.
+  template <int GW>
+  __device__ __forceinline__ int decode_table(const TableScratch& ws, int lane) {
+    const uint32_t slot = x & 0xFFFFu;
+    const int s = table_search<GW>(ws, slot, lane);
+    advance(slot, cum_at<GW>(ws, s), cum_at<GW>(ws, s + 1));
     return s;
   }
 };

@@ -177,3 +177,35 @@ def test_oracle_decodes_same_partition_same_pixels():
     # one stream each: the payloads differ only through FP32 vs FP64 tables
     assert abs((int(offs[1]) - 36) - len(words)) <= 16
     assert 8 * len(words) <= bq + 32 + 1
+
+
+@pytest.mark.parametrize("prec", [N.NLC_FP32, N.NLC_BF16])
+def test_streams_equal_oracle_rans_on_gpu_tables(prec):
+    # the container's per-row streams are byte-identical to the oracle's rANS
+    # encoder fed the GPU's own tables (nlc_tables over nlc_forward's outputs)
+    cfg = (2, 32, 1, 10)
+    codec, _ = make_codec(cfg, prec, seed=12)
+    img = images(17, [(20, 36)])[0]
+    H, W = img.shape[:2]
+    d = to_dev(img)
+    data, offs = codec.compress([d], 0, 1)
+    P, _ = codec.forward([d], 0)
+    cum = codec.tables(P, d.reshape(-1, 3)).cpu().numpy().astype(np.int64)
+    _check_increasing(cum)
+    v = img.reshape(-1, 3).astype(np.int64)
+    px, ch = np.arange(len(v))[:, None], np.arange(3)[None, :]
+    start = cum[px, ch, v]
+    freq = cum[px, ch, v + 1] - start
+    buf = data.cpu().numpy()[int(offs[0]):int(offs[1])]
+    lens = buf[32:32 + 4 * H].copy().view("<u4")
+    pos = 32 + 4 * H
+    for r in range(H):
+        rows = slice(r * W, (r + 1) * W)
+        ref = O.rans_encode(start[rows].reshape(-1), freq[rows].reshape(-1))
+        assert np.array_equal(buf[pos:pos + int(lens[r])], ref), r
+        pos += int(lens[r])
+
+
+def _check_increasing(cum):
+    assert (cum[..., 0] == 0).all() and (cum[..., 256] == 65536).all()
+    assert (np.diff(cum, axis=-1) >= 1).all()
