@@ -383,8 +383,9 @@ def main():
         extra["train"] = {"steps": args.train_steps, "seconds": train_s, "final_loss_bpd": train_loss}
 
     peaks, src = _measured_peaks()
-    # roofline of the decode kernel: MUFU-bound CDF evaluation
-    evals_per_px = 3 * 255 * CFG[3]
+    # roofline of the decode kernel: MUFU work of the symbol search, two
+    # rounds of 15 boundaries x K logistic terms (ex2 + rcp) per channel
+    evals_per_px = 3 * 2 * 15 * CFG[3]
     mufu_ops = 2.0 * evals_per_px * n_px
     clk = clk.summary()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -394,6 +395,7 @@ def main():
     roof = {"bound": "alu", "unit": "MUFU op/s", "achieved": achieved, "peak": mufu_peak,
             "frac": achieved / mufu_peak, "traffic": None,
             "peak_source": f"16 MUFU lanes/clk/SM x 152 SMs x {sm_mhz:.0f} MHz (max SM clock)",
+            "work": f"{2 * evals_per_px} MUFU ops/px (search terms only)",
             "tensor": {"achieved_tflops": flops / (ms / 1e3) / 1e12,
                        "peak_tflops": peaks.get("bf16_tflops_sustained"),
                        "frac": flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops_sustained", 1700),

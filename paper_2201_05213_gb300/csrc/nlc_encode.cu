@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane < K) {
           l = cs.logpi;
           for (int ch = 0; ch < 3; ch++)
-            l = __fadd_rn(l, log_bin_mass_f(comp_mean(cs, ch, v[0], v[1]), cs.ls[ch], v[ch]));
+            l = __fadd_rn(l, log_bin_mass_f(comp_mean(cs, ch, v[0], v[1]), cs.inv[ch],
+                                             cs.lme[ch], v[ch]));
         }
         float mx = l;
 #pragma unroll

@@ -229,23 +229,44 @@ __device__ __forceinline__ float log_f(float x) { return __fmul_rn(lg2_approx(x)
 __device__ __forceinline__ float softplus_f(float x) {
   return __fadd_rn(fmaxf(x, 0.f), log_f(__fadd_rn(1.f, exp_f(-fabsf(x)))));
 }
-// log(1 - e^{-d}), d > 0 (accurate expm1 for small d, Maechler 2012)
+// log(1 - e^{-d}), d > 0.  For d < 1/8 the Taylor series
+// 1 - e^{-d} = d (1 - d/2 + d^2/6 - d^3/24 + d^4/120) (relative error below
+// 5e-8 there) avoids the cancellation of 1 - e^{-d}.
 __device__ __forceinline__ float log1mexp_f(float d) {
-  return d <= 0.6931471805599453f ? log_f(-expm1f(-d)) : log_f(__fsub_rn(1.f, exp_f(-d)));
+  if (d < 0.125f) {
+    float p = __fmaf_rn(d, 1.f / 120.f, -1.f / 24.f);
+    p = __fmaf_rn(p, d, 1.f / 6.f);
+    p = __fmaf_rn(p, d, -0.5f);
+    p = __fmaf_rn(p, d, 1.f);
+    return log_f(__fmul_rn(d, p));
+  }
+  return log_f(__fsub_rn(1.f, exp_f(-d)));
 }
 
-// log P(v) of one logistic component, stable in both tails:
+// log(1 - e^{-d}) of a component with log-scale ls and inv = e^{-ls}, where
+// d = (2/255) inv is the bin width over the scale; for d < e^-14 it is taken
+// as log d = log(2/255) - ls (error O(d)), which stays finite when inv
+// underflows.
+__device__ __forceinline__ float bin_log_width(float ls, float inv) {
+  const float logd = __fsub_rn(-4.848116f, ls);
+  return logd < -14.f ? logd : log1mexp_f(__fmul_rn(2.f * kInv255, inv));
+}
+
+// tanh x = sign(x) (1 - 2/(1 + e^{2|x|})), |x| capped at 20 (tanh = 1 in FP32).
+__device__ __forceinline__ float tanh_f(float x) {
+  const float ax = fminf(fabsf(x), 20.f);
+  const float r = rcp_approx(__fadd_rn(1.f, exp_f(__fmul_rn(2.f, ax))));
+  return copysignf(__fsub_rn(1.f, __fmul_rn(2.f, r)), x);
+}
+
+// log P(v) of one logistic component with location m, inv = e^{-ls} and
+// lme = bin_log_width(ls, inv), stable in both tails:
 // log P = -softplus(-a) - softplus(b) + log(1 - e^{-(a-b)}), a - b = (2/255)/s.
-__device__ __forceinline__ float log_bin_mass_f(float m, float ls, int v) {
-  const float inv = exp_f(-ls);
+__device__ __forceinline__ float log_bin_mass_f(float m, float inv, float lme, int v) {
   if (v <= 0) return -softplus_f(-__fmul_rn(__fsub_rn(edge_f(1), m), inv));
   if (v >= 255) return -softplus_f(__fmul_rn(__fsub_rn(edge_f(255), m), inv));
   const float a = __fmul_rn(__fsub_rn(edge_f(v + 1), m), inv);
   const float b = __fmul_rn(__fsub_rn(edge_f(v), m), inv);
-  // d = (2/255) e^{-ls}; for d < e^-14 log(1 - e^{-d}) = log d + O(d) is taken
-  // in the log domain, which stays finite when e^{-ls} underflows
-  const float logd = __fsub_rn(-4.848116f, ls);
-  const float lme = logd < -14.f ? logd : log1mexp_f(__fmul_rn(2.f * kInv255, inv));
   return __fadd_rn(__fsub_rn(-softplus_f(-a), softplus_f(b)), lme);
 }
 
@@ -315,8 +336,10 @@ __device__ __forceinline__ uint32_t cum_at(const TableScratch& ws, int b) {
 // Per-pixel mixture state held by lane k (< K) for component k.
 struct CompState {
   float logpi, lw;      // log pi_k, running log weight
-  float mu[3], ls[3], co[3];
-  float c[3];           // log2(e) / s_{c,k}
+  float mu[3], co[3];   // locations, coupling coefficients (tanh)
+  float inv[3];         // 1/s = e^{-ls} (log-scale ls clamped at -7)
+  float c[3];           // log2(e) / s
+  float lme[3];         // bin_log_width(ls, 1/s)
 };
 
 template <int GW = 32>
@@ -332,9 +355,11 @@ __device__ __forceinline__ void comp_init(const float* P, int K, int gl, CompSta
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       cs.mu[c] = P[K + c * K + gl];
-      cs.ls[c] = fmaxf(P[4 * K + c * K + gl], -7.f);
-      cs.co[c] = tanhf(P[7 * K + c * K + gl]);
-      cs.c[c] = __fmul_rn(exp_f(-cs.ls[c]), kLog2e);
+      const float ls = fmaxf(P[4 * K + c * K + gl], -7.f);
+      cs.co[c] = tanh_f(P[7 * K + c * K + gl]);
+      cs.inv[c] = exp_f(-ls);
+      cs.c[c] = __fmul_rn(cs.inv[c], kLog2e);
+      cs.lme[c] = bin_log_width(ls, cs.inv[c]);
     }
   }
 }
@@ -416,7 +441,7 @@ __device__ __forceinline__ float channel_setup(const CompState& cs, int K, int c
   float m = 0.f, wk = 0.f;
   if (gl < K) {
     m = comp_mean(cs, ch, r, g);
-    wk = __fdiv_rn(e, s);
+    wk = fminf(__fmul_rn(e, rcp_approx(s)), 1.f);
   }
   // the weights sum to one, so at least one component is active
   const bool on = gl < K && wk >= kWmin;
@@ -494,7 +519,7 @@ __device__ __forceinline__ int table_search(const TableScratch& ws, uint32_t slo
 
 // Posterior update after channel ch took value v (lanes < K).
 __device__ __forceinline__ void comp_observe(CompState& cs, int K, int ch, float m, int v, int gl) {
-  if (gl < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, cs.ls[ch], v));
+  if (gl < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, cs.inv[ch], cs.lme[ch], v));
 }
 
 }  // namespace nlc

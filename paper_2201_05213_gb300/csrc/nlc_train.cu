@@ -107,9 +107,9 @@ __device__ float pixel_nll_grad(const float* P, int K, int r, int g, int b, floa
   if (lane < K) {
     l = cs.logpi;
     for (int c = 0; c < 3; c++) {
-      const float mc = comp_mean(cs, c, r, g), ls = cs.ls[c], inv = expf(-ls);
+      const float mc = comp_mean(cs, c, r, g), inv = cs.inv[c];
       mm[c] = mc;
-      l = __fadd_rn(l, log_bin_mass_f(mc, ls, v[c]));
+      l = __fadd_rn(l, log_bin_mass_f(mc, inv, cs.lme[c], v[c]));
       if (v[c] == 0) {
         const float a = __fmul_rn(__fsub_rn(edge_f(1), mc), inv);
         const float sa = 1.f / (1.f + expf(a));  // sigmoid(-a)
