@@ -19,6 +19,7 @@ oracle decoder timed on a bounded sample on the host cores.
 from __future__ import annotations
 
 import argparse
+import glob
 import json
 import os
 import subprocess
@@ -52,6 +53,24 @@ def workload_name():
         imgs[s] = imgs.get(s, 0) + 1
     desc = " + ".join(f"{n}x{h}^2" if h == w else f"{n}x{h}x{w}" for (h, w), n in imgs.items())
     return f"{desc} RGB, 256^2 patches, h=3 C=64 R=2 K=10, BF16 net"
+
+
+# DRAM traffic of decode_kernel per decoded pixel from one ncu capture of the
+# small case (1x1024^2: 6.61 MB read + 0.88 MB written for 1,048,576 px), scaled
+# to a launch by its pixels.  It holds only for the kernel sources it was taken
+# on: TRAFFIC_SRC_SHA is their sha256, and any other sources report null.
+TRAFFIC_B_PER_PX = 7.14
+TRAFFIC_SRC_SHA = "0e5c239c1bcd0e10e9f21f397e54fd115bfb3b4658fe2d9fd096107453025aaf"
+
+
+def _csrc_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2201_05213_gb300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def _measured_peaks():
@@ -393,7 +412,10 @@ def main():
     achieved = mufu_ops / (ms / 1e3)
     flops = 54784.0 * n_px
     roof = {"bound": "alu", "unit": "MUFU op/s", "achieved": achieved, "peak": mufu_peak,
-            "frac": achieved / mufu_peak, "traffic": None,
+            "frac": achieved / mufu_peak,
+            "traffic": TRAFFIC_B_PER_PX * n_px if _csrc_sha() == TRAFFIC_SRC_SHA else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 1x1024^2 "
+                              "decode, scaled by pixels (bytes per launch)",
             "peak_source": f"16 MUFU lanes/clk/SM x 152 SMs x {sm_mhz:.0f} MHz (max SM clock)",
             "work": f"{2 * evals_per_px} MUFU ops/px (search terms only)",
             "tensor": {"achieved_tflops": flops / (ms / 1e3) / 1e12,
