@@ -247,6 +247,7 @@ def main():
     __graft_entry__.build()
     from paper_2201_05213_gb300 import codec as CD
     from paper_2201_05213_gb300 import nlc as N
+    from paper_2201_05213_gb300 import shard
     from paper_2201_05213_gb300 import synth
 
     dev = torch.device("cuda", local)
@@ -302,11 +303,7 @@ def main():
             times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     codec.check()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = shard.max_over_ranks(float(np.mean(times)), dev)
     value = world * n_px / (ms / 1e3)
 
     # per-step latency against the dependency-bound step count (untimed run)
@@ -352,7 +349,7 @@ def main():
     codec.check()
     for a, b in zip(h_outs, imgs):
         assert np.array_equal(a.numpy(), b), "end-to-end round trip differs"
-    e2e_ms = float(np.mean(e2e_times))
+    e2e_ms = shard.max_over_ranks(float(np.mean(e2e_times)), dev)
 
     # code lengths
     _, bits = codec.forward(dimgs, PATCH, params=False, bits=True)
