@@ -318,7 +318,10 @@ def main():
     npx0 = max(float(cnt[12]), 1.0)
     coding_us = {name: float(cnt[8 + i]) / npx0 / mhz
                  for i, name in enumerate(["setup", "cdf_search", "rans", "posterior"])}
+    net_us = {name: float(cnt[13 + i]) / ctas / steps_T / mhz
+              for i, name in enumerate(["gather", "mma", "epilogue"])}
     phases = {"steps": steps_T, "ctas": ctas, "tiles_per_cta_step": float(cnt[5]) / ctas / steps_T,
+              "network_us_per_step": net_us,
               "us_per_step_measured": 1000.0 * ms / steps_T,
               "us_per_step_by_phase_at_2070MHz": phase_us,
               "coding_us_per_pixel_warp0": coding_us}

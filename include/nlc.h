@@ -144,7 +144,9 @@ int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
  *   [5] tiles processed, [6] CTAs, [7] decode steps (of CTA 0);
  *   within [3], for the pixels coded by warp 0: [8] mixture and channel
  *   set-up, [9] CDF symbol search, [10] rANS state update, [11] posterior
- *   update, [12] pixels; [13..15] zero.
+ *   update, [12] pixels; within [2], for thread 0 (BF16 network): [13]
+ *   context gather, [14] tensor-core MMA issue to completion, [15] epilogues
+ *   (TMEM loads, bias/ELU, operand stores, CTA barriers).
  * Synchronises the device when reading or changing the mode. */
 int nlc_decode_profile(nlc_ctx* ctx, int enable, uint64_t* h_counters);
 

@@ -80,7 +80,7 @@ static Dims make_dims(const nlc_model_cfg* c) {
   d.Fp = (d.F + 15) / 16 * 16;
   d.NO = 10 * c->K;
   d.NOp = (d.NO + 15) / 16 * 16;
-  d.ldP = d.NOp + 4;
+  d.ldP = d.NOp + 1;  // odd: one pixel per lane stores its row without bank conflicts
   d.prec = c->precision;
   return d;
 }

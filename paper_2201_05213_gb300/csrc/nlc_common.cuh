@@ -38,8 +38,8 @@ enum Schedule { SCHED_RASTER = 0, SCHED_WAVEFRONT = 1 };
 
 // Model dimensions.  F = 6h(h+1) context features (2h(h+1) pixels x RGB),
 // Fp = F rounded up to a multiple of 16, NO = 10K network outputs, NOp = NO
-// rounded up to a multiple of 16, ldP = NOp + 4 (row stride of the per-pixel
-// outputs in shared memory, padded against bank conflicts).
+// rounded up to a multiple of 16, ldP = NOp + 1 (row stride of the per-pixel
+// outputs in shared memory; odd, against bank conflicts).
 struct Dims {
   int h, C, R, K;
   int F, Fp, NO, NOp, ldP;

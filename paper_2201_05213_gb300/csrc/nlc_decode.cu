@@ -25,29 +25,41 @@ struct DecodeArgs {
   unsigned long long* prof;  // optional per-phase cycle counters
 };
 
-// Slot of the warp's l-th pixel when coding groups have GW lanes
-// (32 / GW groups per warp, group g of warp w takes slots g + 32/GW (w + 8 j)).
-template <int GW>
+// Threads of the decoder's CTA: the BF16 pipeline runs 16 warps (32 coding
+// groups of 16 lanes); the FP32 SIMT network is written for 256 threads.
+template <int PREC>
+__host__ __device__ constexpr int decode_threads() { return PREC == PREC_BF16 ? 512 : kThreads; }
+
+// Slot of the warp's l-th pixel when coding groups have GW lanes and the
+// CTA has NW warps (32 / GW groups per warp, group g of warp w takes slots
+// g + 32/GW (w + NW j)).
+template <int GW, int NW>
 __device__ __forceinline__ int group_slot(int warp, int l) {
   constexpr int gpw = 32 / GW;
-  return gpw * warp + (l % gpw) + kWarps * gpw * (l / gpw);
+  return gpw * warp + (l % gpw) + NW * gpw * (l / gpw);
 }
 
-// Codes the tile's pixels: per pixel, the R, G|r, B|r,g tables and one rANS
-// symbol each.  pd holds (in lane l) the prefetched stream state of the
-// warp's l-th pixel.
-template <int GW>
+// Codes the tile's pixels: per pixel, the R, G|r, B|r,g symbols.  pd holds
+// (in lane l) the prefetched stream state of the warp's l-th pixel.  With pc
+// non-null, thread 0 accumulates its sub-stage cycles in pc[8..12].
+template <int GW, int NW>
 __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, int n,
-                                       const GroupRansDec& pd) {
+                                       const GroupRansDec& pd, long long* pc) {
   constexpr int gpw = 32 / GW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / GW, gl = lane % GW;
   const int K = a.m.d.K, ldP = a.m.d.ldP;
-  // sub-stage cycles of thread 0: mixture set-up, tables, rANS, posterior
-  const bool prof = a.prof != nullptr && threadIdx.x == 0;
-  long long s_init = 0, s_tab = 0, s_dec = 0, s_obs = 0, s_px = 0, c0 = 0, c1 = 0;
-  for (int j = 0; gpw * warp + kWarps * gpw * j < n; j++) {
-    const int s = gpw * warp + grp + kWarps * gpw * j;
+  const bool pr = pc != nullptr && threadIdx.x == 0;
+  long long ck = 0;
+  auto tick = [&](int slot) {
+    if (pr) {
+      const long long n_ = clock64();
+      pc[slot] += n_ - ck;
+      ck = n_;
+    }
+  };
+  for (int j = 0; gpw * warp + NW * gpw * j < n; j++) {
+    const int s = gpw * warp + grp + NW * gpw * j;
     const bool valid = s < n;
     const int se = valid ? s : s - 1;  // an idle group shadows its neighbour
     const int src = gpw * j + grp;
@@ -60,33 +72,35 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
     dec.used = 0;
     dec.bad = false;
     const PixSlot ps = t.slots[se];
-    const Unit U = a.units[ps.unit];
-    const int sid = ps.aux;
     WarpScratch& ws = t.ws[gpw * warp + grp];
     CompState cs;
-    if (prof) c0 = clock64();
+    if (pr) {
+      ck = clock64();
+      pc[12] += 1;
+    }
     comp_init<GW>(t.U0 + (size_t)se * ldP, K, gl, cs);
-    if (prof) { c1 = clock64(); s_init += c1 - c0; c0 = c1; s_px++; }
     int v[3] = {0, 0, 0};
     for (int ch = 0; ch < 3; ch++) {
       int nact;
       const float mloc = channel_setup<GW>(cs, K, ch, v[0], v[1], gl, ws, nact);
-      if (prof) { c1 = clock64(); s_init += c1 - c0; c0 = c1; }
+      tick(8);
       const uint32_t slot = dec.x & 0xFFFFu;
       uint32_t lo, hi;
       v[ch] = cdf_search<GW>(ws, nact, slot, gl, lo, hi);
-      if (prof) { c1 = clock64(); s_tab += c1 - c0; c0 = c1; }
+      tick(9);
       dec.advance(slot, lo, hi);
-      if (prof) { c1 = clock64(); s_dec += c1 - c0; c0 = c1; }
+      tick(10);
       if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
       __syncwarp();
-      if (prof) { c1 = clock64(); s_obs += c1 - c0; c0 = c1; }
+      tick(11);
     }
     if (gl == 0 && valid) {
+      const Unit U = a.units[ps.unit];
       uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
       px[0] = (uint8_t)v[0];
       px[1] = (uint8_t)v[1];
       px[2] = (uint8_t)v[2];
+      const int sid = ps.aux;
       const unsigned long long np = dec.pos + (unsigned long long)dec.used;
       a.st_x[sid] = dec.x;
       a.st_pos[sid] = np;
@@ -94,37 +108,41 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       if (dec.bad || (last && (dec.x != kRansL || np != dec.end))) set_status(a.status, ST_CORRUPT);
     }
   }
-  if (prof) {
-    atomicAdd(a.prof + 8, (unsigned long long)s_init);
-    atomicAdd(a.prof + 9, (unsigned long long)s_tab);
-    atomicAdd(a.prof + 10, (unsigned long long)s_dec);
-    atomicAdd(a.prof + 11, (unsigned long long)s_obs);
-    atomicAdd(a.prof + 12, (unsigned long long)s_px);
-  }
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
+__global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(DecodeArgs a) {
+  constexpr int NT = decode_threads<PREC>(), NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
   const Dims& d = a.m.d;
-  TileSmem t = carve(d, smem, a.n_units);
+  TileSmem t = carve(d, smem, a.n_units, NT / kGW);
   if constexpr (PREC == PREC_BF16) tc_setup(t.tc);
   load_weights<PREC>(a.m, t);
   if (threadIdx.x == 0) t.flag[0] = 0;
+  if (threadIdx.x < 16) t.pc[threadIdx.x] = 0;
   __syncthreads();
   constexpr int MT = tile_size<PREC>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int h = d.h;
   unsigned my_gen = 0;
   const unsigned G = gridDim.x;
-  // phase cycles of thread 0: front scan, slot fill, gather + network,
-  // per-pixel coding, grid barrier
-  const bool prof = a.prof != nullptr && threadIdx.x == 0;
-  long long ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, tiles = 0, tc = 0, tn = 0;
+  // phase cycles of thread 0 (shared-memory accumulators): [0] front scan,
+  // [1] slot fill, [2] gather + network, [3] per-pixel coding, [4] grid
+  // barrier, [5] tiles
+  long long* pc = a.prof != nullptr ? t.pc : nullptr;
+  const bool pr = pc != nullptr && threadIdx.x == 0;
+  long long ck = 0;
+  auto tick = [&](int slot) {
+    if (pr) {
+      const long long n_ = clock64();
+      pc[slot] += n_ - ck;
+      ck = n_;
+    }
+  };
   for (int step = 0; step < a.T; step++) {
-    if (prof) tc = clock64();
+    if (pr) ck = clock64();
     const int F = front_scan(a.units, a.n_units, step, h, a.sched, t.pre, t.sh);
-    if (prof) { tn = clock64(); ph0 += tn - tc; tc = tn; }
+    tick(0);
     const long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
     for (long long base = lo; base < hi; base += MT) {
       const int n = (int)min((long long)MT, hi - base);
@@ -149,15 +167,15 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
       __syncthreads();
       // A CTA with at most one pixel per warp codes with whole warps (lower
       // latency per pixel); otherwise two pixels per warp.  Both give the
-      // same tables (see channel_table).  Lane l of warp w fetches the rANS
-      // state and next 8 bytes of the warp's l-th pixel ahead of the network.
-      const bool wide = n <= kWarps;
+      // same tables (see cdf_fix).  Lane l of warp w fetches the rANS state
+      // and next 8 bytes of the warp's l-th pixel ahead of the network.
+      const bool wide = n <= NW;
       GroupRansDec pd;
       pd.x = 0;
       pd.pos = pd.end = 0;
       pd.lo = pd.hi = 0;
       {
-        const int sl = wide ? group_slot<32>(warp, lane) : group_slot<kGW>(warp, lane);
+        const int sl = wide ? group_slot<32, NW>(warp, lane) : group_slot<kGW, NW>(warp, lane);
         if (sl < n) {
           const int sid = t.slots[sl].aux;
           pd.x = ld_cg_u32(a.st_x + sid);
@@ -166,35 +184,38 @@ __global__ void __launch_bounds__(kThreads, 1) decode_kernel(DecodeArgs a) {
           pd.load_bytes(a.in);
         }
       }
-      if (prof) { tn = clock64(); ph1 += tn - tc; tc = tn; tiles++; }
-      tile_network<PREC, true>(a.m, a.units, t, n);
-      if (prof) { tn = clock64(); ph2 += tn - tc; tc = tn; }
-      if (wide) code_tile<32>(a, t, n, pd);
-      else code_tile<kGW>(a, t, n, pd);
+      if (pr) pc[5] += 1;
+      tick(1);
+      tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+      tick(2);
+      if (wide) code_tile<32, NW>(a, t, n, pd, pc);
+      else code_tile<kGW, NW>(a, t, n, pd, pc);
       __syncthreads();
-      if (prof) { tn = clock64(); ph3 += tn - tc; tc = tn; }
+      tick(3);
     }
     if (G > 1) {
       if (!grid_barrier(a.bar, a.bar + 1, G, my_gen, a.status, t.flag)) break;
     } else {
       __syncthreads();
     }
-    if (prof) ph4 += clock64() - tc;
+    tick(4);
   }
-  if (prof) {
-    atomicAdd(a.prof + 0, (unsigned long long)ph0);
-    atomicAdd(a.prof + 1, (unsigned long long)ph1);
-    atomicAdd(a.prof + 2, (unsigned long long)ph2);
-    atomicAdd(a.prof + 3, (unsigned long long)ph3);
-    atomicAdd(a.prof + 4, (unsigned long long)ph4);
-    atomicAdd(a.prof + 5, (unsigned long long)tiles);
+  if (pr) {
+    for (int i = 0; i < 16; i++)
+      if (i != 6 && i != 7) atomicAdd(a.prof + i, (unsigned long long)pc[i]);
     atomicAdd(a.prof + 6, 1ull);
     if (blockIdx.x == 0) atomicAdd(a.prof + 7, (unsigned long long)a.T);
   }
   if constexpr (PREC == PREC_BF16) tc_teardown(t.tc);
 }
 
-size_t decode_smem_bytes(const Dims& d, int n_units) { return tile_smem_bytes(d, n_units); }
+static int decode_threads_of(int prec) {
+  return prec == PREC_BF16 ? decode_threads<PREC_BF16>() : decode_threads<PREC_FP32>();
+}
+
+size_t decode_smem_bytes(const Dims& d, int n_units) {
+  return tile_smem_bytes(d, n_units, decode_threads_of(d.prec) / kGW);
+}
 
 static const void* decode_fn(int prec) {
   return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16>
@@ -208,7 +229,8 @@ int decode_max_grid(const DeviceModel& m, int n_units, int sm_count) {
       cudaSuccess)
     return 0;
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, decode_threads_of(m.d.prec), smem) !=
+      cudaSuccess)
     return 0;
   return per * sm_count;
 }
@@ -237,12 +259,13 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   a.prof = b.prof;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
   const void* fn = decode_fn(m.d.prec);
+  const int nt = decode_threads_of(m.d.prec);
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return e;
   void* args[] = {&a};
-  if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
-  return cudaLaunchKernel(fn, dim3(1), dim3(kThreads), args, smem, s);
+  if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(nt), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(1), dim3(nt), args, smem, s);
 }
 
 }  // namespace nlc

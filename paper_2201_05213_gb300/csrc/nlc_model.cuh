@@ -289,6 +289,18 @@ struct TableScratch {
 // they move 65280 F(b) by at most half a count per component.
 constexpr float kWmin = 7.62939453125e-06f;
 
+// Fixed point with 23 fraction bits: x in [0, 2^23] plus 2^23, rounded to
+// nearest, is 2^23 + rint(x) (the spacing of floats in [2^23, 2^24] is 1);
+// its bit pattern minus that of 2^23 is rint(x).
+constexpr float kFixOne = 8388608.f;           // 2^23
+constexpr uint32_t kFixOneBits = 0x4B000000u;  // bit pattern of 2^23
+constexpr float kLn2x23 = 15.942385152878742f;  // 23 ln 2
+
+// rint(e 2^23) for e in [0, 1].
+__device__ __forceinline__ uint32_t fix23(float e) {
+  return (uint32_t)__float_as_int(__fadd_rn(__fmul_rn(e, kFixOne), kFixOne)) - kFixOneBits;
+}
+
 // ---------------------------------------------------------------------
 // Coding groups.  One pixel's channels are coded by a group of GW lanes
 // (GW = 32: a whole warp; GW = 16: half a warp, so that a warp codes two
@@ -312,6 +324,32 @@ __device__ __forceinline__ float grp_sum(float v) {
 template <int GW>
 __device__ __forceinline__ unsigned grp_mask(int lane) {
   return GW == 32 ? 0xffffffffu : (0xFFFFu << (lane & 16));
+}
+// Exact group maximum of floats and exact group sum of integers.  A whole
+// warp uses redux.sync (the maximum on order-preserving integer keys:
+// negative floats get their magnitude bits flipped); a 16-lane group uses
+// xor butterflies, because redux.sync with a mask per half warp is slower
+// than the butterfly.  Both forms give the same value.
+template <int GW>
+__device__ __forceinline__ float grp_max_r(float v) {
+  if constexpr (GW == 32) {
+    int k = __float_as_int(v);
+    k = k >= 0 ? k : k ^ 0x7FFFFFFF;
+    k = __reduce_max_sync(0xffffffffu, k);
+    return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF);
+  } else {
+    return grp_max<GW>(v);
+  }
+}
+template <int GW>
+__device__ __forceinline__ uint32_t grp_isum(uint32_t v) {
+  if constexpr (GW == 32) {
+    return __reduce_add_sync(0xffffffffu, v);
+  } else {
+#pragma unroll
+    for (int o = GW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, GW);
+    return v;
+  }
 }
 // The group's bits of a warp ballot, group lane 0 in bit 0.
 template <int GW>
@@ -344,11 +382,13 @@ struct CompState {
 
 template <int GW = 32>
 __device__ __forceinline__ void comp_init(const float* P, int K, int gl, CompState& cs) {
+  // log-sum-exp of the logits: exact max, then the sum of e^{logit - max}
+  // in fixed point (an exact integer sum, S >= 2^23 from the max itself)
   const float logit = gl < K ? P[gl] : -INFINITY;
-  const float mx = grp_max<GW>(logit);
-  const float e = gl < K ? exp_f(__fsub_rn(logit, mx)) : 0.f;
-  const float s = grp_sum<GW>(e);
-  const float lse = __fadd_rn(mx, log_f(s));
+  const float mx = grp_max_r<GW>(logit);
+  const uint32_t E = fix23(gl < K ? exp_f(__fsub_rn(logit, mx)) : 0.f);
+  const uint32_t S = grp_isum<GW>(E);
+  const float lse = __fadd_rn(mx, __fsub_rn(log_f((float)S), kLn2x23));
   cs.logpi = __fsub_rn(logit, lse);
   cs.lw = cs.logpi;
   if (gl < K) {
@@ -386,9 +426,7 @@ __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, i
 // lanes, in the encoder, the decoder or the table entry point, gives the
 // same cum_b.
 // ---------------------------------------------------------------------
-constexpr float kFixOne = 8388608.f;           // 2^23
-constexpr uint32_t kFixOneBits = 0x4B000000u;  // bit pattern of 2^23
-constexpr float kZMax = 126.f;                 // |z| clamp of the logistic's 2^z
+constexpr float kZMax = 126.f;  // |z| clamp of the logistic's 2^z
 
 // One component's term of F at boundary value e: the logistic is
 // 1/(1 + 2^z) with z = (m - e) log2(e)/s clamped to [-126, 126], and
@@ -434,22 +472,27 @@ __device__ __forceinline__ uint32_t cum_fix(uint32_t Fi, int b) {
 template <int GW>
 __device__ __forceinline__ float channel_setup(const CompState& cs, int K, int ch, int r, int g,
                                                int gl, WarpScratch& ws, int& nact) {
-  const float lw = gl < K ? cs.lw : -INFINITY;
-  const float mx = grp_max<GW>(lw);
-  const float e = gl < K ? exp_f(__fsub_rn(lw, mx)) : 0.f;
-  const float s = grp_sum<GW>(e);
-  float m = 0.f, wk = 0.f;
-  if (gl < K) {
-    m = comp_mean(cs, ch, r, g);
-    wk = fminf(__fmul_rn(e, rcp_approx(s)), 1.f);
+  // w_k 2^23: for R the mixture weights pi_k = e^{log pi_k} (normalised by
+  // comp_init); for G and B the posterior e^{lw_k - max} / sum, the sum taken
+  // exactly in fixed point
+  float wS = 0.f;
+  if (ch == 0) {
+    if (gl < K) wS = __fmul_rn(fminf(exp_f(cs.logpi), 1.f), kFixOne);
+  } else {
+    const float lw = gl < K ? cs.lw : -INFINITY;
+    const float mx = grp_max_r<GW>(lw);
+    const uint32_t E = fix23(gl < K ? exp_f(__fsub_rn(lw, mx)) : 0.f);
+    const uint32_t S = grp_isum<GW>(E);
+    wS = fminf(__fmul_rn((float)E, __fmul_rn(kFixOne, rcp_approx((float)S))), kFixOne);
   }
+  const float m = gl < K ? comp_mean(cs, ch, r, g) : 0.f;
   // the weights sum to one, so at least one component is active
-  const bool on = gl < K && wk >= kWmin;
+  const bool on = gl < K && wS >= kWmin * kFixOne;
   const unsigned bits = grp_ballot<GW>(on);
   nact = __popc(bits);
   for (int p = gl; p < 2 * kMaxK; p += GW)
     if (p >= nact) ws.cp[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (on) ws.cp[__popc(bits & ((1u << gl) - 1u))] = make_float4(m, cs.c[ch], __fmul_rn(wk, kFixOne), 0.f);
+  if (on) ws.cp[__popc(bits & ((1u << gl) - 1u))] = make_float4(m, cs.c[ch], wS, 0.f);
   __syncwarp();
   return m;
 }

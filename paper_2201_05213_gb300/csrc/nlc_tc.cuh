@@ -266,54 +266,66 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // --- gather ------------------------------------------------------------------
-// X(m, k) = 2v - 255 for feature k = 3p + c of tap p, 0 outside the unit,
-// for k >= F and for empty slots.  Each thread writes 16-byte chunks.
+// X(m, k) = 2v - 255 for feature k = 3p + c of tap p, 0 outside the unit and
+// for F <= k < Fp.  One lane per (pixel m, context row r): row r < h is image
+// row i - h + r over columns j-h .. j+h, row h is row i over columns j-h ..
+// j-1 (the taps of Eq. 3 in raster order).  A row's 3(2h+1) (or 3h) bytes are
+// contiguous in the image and are features k0 = 3 r (2h+1) onwards, so the
+// lane reads the aligned 32-bit words that hold at least one byte of the row
+// inside the unit (never a word without a byte of the image), realigns them
+// with funnel shifts and writes the features.  A warp covers 8 pixels x 4
+// rows, so the four rows' stores of one feature index fall on different banks.
 template <bool kCoherent>
 __device__ __noinline__ void tc_gather(const Unit* units, const PixSlot* slots, const Dims& d,
                                        TcSmem& t, int n_valid) {
-  // (pixel, tap) pairs of the valid rows; each thread issues all its context
-  // loads before any shared-memory store.  Rows >= n_valid are left as they
-  // are: tensor-core rows are independent and their outputs are not read.
-  constexpr int kMaxPairs = (kTcM * 2 * kMaxH * (kMaxH + 1) + kThreads - 1) / kThreads;
-  const int Fp = d.Fp, F = d.F, h = d.h, w2 = 2 * h + 1, ntap = 2 * h * (h + 1);
-  const int npairs = n_valid * ntap;
-  uint32_t val[kMaxPairs];
+  const int h = d.h, Fp = d.Fp, F = d.F, w2 = 2 * h + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane >> 3;
+  for (int mb = 8 * warp; mb < n_valid; mb += 8 * (int)(blockDim.x >> 5)) {
+    const int m = mb + (lane & 7);
+    if (r > h || m >= n_valid) continue;
+    const PixSlot s = slots[m];
+    const Unit u = units[s.unit];
+    const int y = r < h ? s.i - h + r : s.i;
+    const int ncol = r < h ? w2 : h;  // pixels of this row's window
+    const int k0 = 3 * r * w2;
+    // window columns x = j - h + c, c in [0, ncol); inside the unit: [ca, cb)
+    const int x0 = s.j - h;
+    const int ca = x0 < 0 ? -x0 : 0;
+    const int cb = min(ncol, u.Wu - x0);
+    const bool row_ok = y >= 0 && y < u.Hu && ca < cb;
+    uint32_t wv[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    uint32_t sh = 0;
+    if (row_ok) {
+      const uintptr_t row = (uintptr_t)(u.img + ((long long)(u.y0 + y) * u.img_W + u.x0) * 3);
+      const uintptr_t lo = row + (uintptr_t)(3 * (long long)x0);  // window start
+      const uintptr_t a = lo + 3 * ca, b = lo + 3 * cb;         // bytes inside the unit
+      const uintptr_t w0 = lo & ~(uintptr_t)3;
+      sh = 8u * (uint32_t)(lo & 3);
 #pragma unroll
-  for (int r = 0; r < kMaxPairs; r++) {
-    const int it = threadIdx.x + r * kThreads;
-    uint32_t v = 0;
-    if (it < npairs) {
-      const int m = it / ntap, p = it - m * ntap;
-      const PixSlot s = slots[m];
-      const Unit u = units[s.unit];
-      const int ii = s.i + p / w2 - h, jj = s.j + p % w2 - h;
-      if (ii >= 0 && ii < u.Hu && jj >= 0 && jj < u.Wu) {
-        const uint8_t* px = u.img + ((long long)(u.y0 + ii) * u.img_W + (u.x0 + jj)) * 3;
-        const uint32_t b0 = kCoherent ? ld_cg_u8(px) : px[0];
-        const uint32_t b1 = kCoherent ? ld_cg_u8(px + 1) : px[1];
-        const uint32_t b2 = kCoherent ? ld_cg_u8(px + 2) : px[2];
-        v = b0 | (b1 << 8) | (b2 << 16) | (1u << 24);
+      for (int q = 0; q < 6; q++) {
+        const uintptr_t wa = w0 + 4 * q;
+        if (wa + 4 > a && wa < b) {
+          const uint32_t* p = reinterpret_cast<const uint32_t*>(wa);
+          wv[q] = kCoherent ? ld_cg_u32(p) : *p;
+        }
       }
     }
-    val[r] = v;
-  }
+    uint32_t al[6];
 #pragma unroll
-  for (int r = 0; r < kMaxPairs; r++) {
-    const int it = threadIdx.x + r * kThreads;
-    if (it < npairs) {
-      const int m = it / ntap, p = it - m * ntap;
-      const uint32_t v = val[r];
+    for (int q = 0; q < 6; q++) al[q] = __funnelshift_r(wv[q], wv[q + 1], sh);
+    uint16_t* X = t.X;
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const float x = (v >> 24) ? (float)(2 * (int)((v >> (8 * c)) & 0xFFu) - 255) : 0.f;
-        t.X[umma_off(m, 3 * p + c, Fp)] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    for (int q = 0; q < 3 * (2 * kMaxH + 1); q++) {
+      const int c = q / 3;
+      if (c < ncol) {
+        const int v = (int)((al[q >> 2] >> (8 * (q & 3))) & 0xFFu);
+        const float x = (row_ok && c >= ca && c < cb) ? (float)(2 * v - 255) : 0.f;
+        X[umma_off(m, k0 + q, Fp)] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
       }
     }
-  }
-  const int npad = Fp - F;
-  for (int it = threadIdx.x; it < n_valid * npad; it += kThreads) {
-    const int m = it / npad, k = F + it % npad;
-    t.X[umma_off(m, k, Fp)] = 0;
+    if (r == h)
+      for (int k = F; k < Fp; k++) X[umma_off(m, k, Fp)] = 0;
   }
 }
 
@@ -354,115 +366,142 @@ __device__ __forceinline__ void store_h8(uint16_t* H, int r, int k0, int C, cons
   *reinterpret_cast<uint4*>(H + umma_off(r, k0, C)) = q;
 }
 
+// 8 consecutive FP32 columns of this thread's TMEM lane, without waiting:
+// the registers hold the values only after tmem_wait_ld() and tmem_touch().
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Orders every use of r after the preceding tmem_wait_ld (the registers pass
+// through an asm that the compiler cannot move above the wait).
+__device__ __forceinline__ void tmem_touch(uint32_t (&r)[8]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]));
+}
+
 // Runs the whole network on the tile in X; P[m][ldP] = head outputs.
-static __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid) {
+//
+// Epilogues: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the
+// 8-column chunks c = w/4, w/4 + NP, ... (NP = NT/128 column parts), issuing
+// all its loads before one wait.  With pc non-null, thread 0 adds its cycles
+// from MMA issue to completion to pc[14] and those of the epilogues (TMEM
+// loads, bias/ELU, operand stores, CTA barriers) to pc[15].
+template <int NT>
+__device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, long long* pc) {
+  constexpr int NP = NT / 128;                // column parts
+  constexpr int CH = (kMaxC / 8 + NP - 1) / NP;  // chunks of the hidden width per thread
+  constexpr int HB = 4;                       // head chunks per load batch
   const TcPlan pl = tc_plan(d);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * (warp & 3) + lane;
+  const int part = warp >> 2;
   // a warp whose 32 TMEM lanes hold no valid pixel skips its epilogue
   const bool live = 32 * (warp & 3) < n_valid;
-  const int half = warp >> 2;
   const uint32_t tl = t.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-  const int C = d.C, ch = C / 2, c0 = half * ch;
-  const float* b0 = t.bias;
-  float a[kMaxC / 2];
+  const int C = d.C, nc = C / 8;
+  float a[CH][8];
   bool ok = true;
+  const bool pr = pc != nullptr && threadIdx.x == 0;
+  long long ck = pr ? clock64() : 0;
+  auto tick = [&](int slot) {
+    if (pr) {
+      const long long n_ = clock64();
+      pc[slot] += n_ - ck;
+      ck = n_;
+    }
+  };
+  // epilogue of a hidden layer: v = acc + bias (+ residual), H = ELU(v)
+  auto hidden = [&](const float* bias, int mode) {  // 0: a = v, 1: a += v, 2: H only
+    if (live) {
+      uint32_t r[CH][8];
+#pragma unroll
+      for (int i = 0; i < CH; i++)
+        if (part + NP * i < nc) tmem_ld8_nw(tl + (uint32_t)(8 * (part + NP * i)), r[i]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < CH; i++) {
+        const int c = part + NP * i;
+        if (c < nc) {
+          tmem_touch(r[i]);
+          float u[8];
+#pragma unroll
+          for (int e = 0; e < 8; e++) {
+            const float v = __fadd_rn(__uint_as_float(r[i][e]), bias[8 * c + e]);
+            if (mode == 0) a[i][e] = v;
+            if (mode == 1) a[i][e] = __fadd_rn(a[i][e], v);
+            u[e] = elu_tc(mode == 2 ? v : a[i][e]);
+          }
+          store_h8(t.H, row, 8 * c, C, u);
+        }
+      }
+    }
+    fence_before_sync();
+    fence_async_smem();
+    __syncthreads();
+  };
 
   // layer 0: a = X W0^T + b0, H = ELU(a)
   fence_async_smem();
   __syncthreads();
+  tick(15);
   tc_issue(t, (uint32_t)pl.p, (uint32_t)pl.w0, d.Fp, C);
   ok &= tc_wait(t);
-  if (live) {
-    float v[32];
-    tmem_ld_cols(tl + (uint32_t)c0, ch, v);
-#pragma unroll
-    for (int g = 0; g < kMaxC / 16; g++) {
-      if (g < ch / 8) {
-        float u[8];
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-          a[8 * g + e] = __fadd_rn(v[8 * g + e], b0[c0 + 8 * g + e]);
-          u[e] = elu_tc(a[8 * g + e]);
-        }
-        store_h8(t.H, row, c0 + 8 * g, C, u);
-      }
-    }
-  }
-  fence_before_sync();
-  fence_async_smem();
-  __syncthreads();
-
+  tick(14);
+  hidden(t.bias, 0);
   for (int r = 0; r < d.R; r++) {
     const float* b1 = t.bias + C + 2 * r * C;
-    const float* b2 = b1 + C;
     // hidden = ELU(H W1^T + b1)
+    tick(15);
     tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w1[r], C, C);
     ok &= tc_wait(t);
-    if (live) {
-      float v[32];
-      tmem_ld_cols(tl + (uint32_t)c0, ch, v);
-#pragma unroll
-      for (int g = 0; g < kMaxC / 16; g++) {
-        if (g < ch / 8) {
-          float u[8];
-#pragma unroll
-          for (int e = 0; e < 8; e++) u[e] = elu_tc(__fadd_rn(v[8 * g + e], b1[c0 + 8 * g + e]));
-          store_h8(t.H, row, c0 + 8 * g, C, u);
-        }
-      }
-    }
-    fence_before_sync();
-    fence_async_smem();
-    __syncthreads();
+    tick(14);
+    hidden(b1, 2);
     // a += H W2^T + b2, H = ELU(a)
+    tick(15);
     tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w2[r], C, C);
     ok &= tc_wait(t);
-    if (live) {
-      float v[32];
-      tmem_ld_cols(tl + (uint32_t)c0, ch, v);
-#pragma unroll
-      for (int g = 0; g < kMaxC / 16; g++) {
-        if (g < ch / 8) {
-          float u[8];
-#pragma unroll
-          for (int e = 0; e < 8; e++) {
-            a[8 * g + e] = __fadd_rn(a[8 * g + e], __fadd_rn(v[8 * g + e], b2[c0 + 8 * g + e]));
-            u[e] = elu_tc(a[8 * g + e]);
-          }
-          store_h8(t.H, row, c0 + 8 * g, C, u);
-        }
-      }
-    }
-    fence_before_sync();
-    fence_async_smem();
-    __syncthreads();
+    tick(14);
+    hidden(b1 + C, 1);
   }
 
-  // head: P = H WH^T + bH
+  // head: P = H WH^T + bH, in batches of HB chunks
   const float* bh = t.bias + C + 2 * d.R * C;
+  tick(15);
   tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.wh, C, d.NOp);
   ok &= tc_wait(t);
-  const int nh = d.NOp / 2, n0 = half * nh;
+  tick(14);
   if (live) {
-    // columns n0 .. n0 + nh - 1 in loads of up to 32 columns
-    for (int c = 0; c < nh; c += 32) {
-      const int cw = nh - c < 32 ? nh - c : 32;
-      float v[32];
-      if (cw == 32) {
-        tmem_ld32(tl + (uint32_t)(n0 + c), v);
-      } else {
-        tmem_ld_cols(tl + (uint32_t)(n0 + c), cw & ~7, v);
-      }
-      float* o = t.P + (size_t)row * d.ldP + n0 + c;
+    const int nh = d.NOp / 8;
+    float* o = t.P + (size_t)row * d.ldP;
+    for (int c0 = part; c0 < nh; c0 += NP * HB) {
+      uint32_t r[HB][8];
 #pragma unroll
-      for (int e = 0; e < 32; e++)
-        if (e < (cw & ~7)) o[e] = __fadd_rn(v[e], bh[n0 + c + e]);
+      for (int i = 0; i < HB; i++)
+        if (c0 + NP * i < nh) tmem_ld8_nw(tl + (uint32_t)(8 * (c0 + NP * i)), r[i]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < HB; i++) {
+        const int c = c0 + NP * i;
+        if (c < nh) {
+          tmem_touch(r[i]);
+#pragma unroll
+          for (int e = 0; e < 8; e++) o[8 * c + e] = __fadd_rn(__uint_as_float(r[i][e]), bh[8 * c + e]);
+        }
+      }
     }
   }
   fence_before_sync();
   __syncthreads();
-  return __syncthreads_and(ok ? 1 : 0) != 0;
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  tick(15);
+  return all_ok;
 }
 
 cudaError_t launch_repack_umma(const Dims& d, const float* w, uint16_t* umma, float* bias,

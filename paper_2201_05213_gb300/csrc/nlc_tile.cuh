@@ -176,11 +176,13 @@ struct TileSmem {
   PixSlot* slots;
   int* pre;
   long long* sh;
+  long long* pc;  // 16 profiling accumulators (thread 0 only)
   int* flag;
   TcSmem tc;
 };
 
-__host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre) {
+// Shared memory of the tile pipeline with `groups` coding groups.
+__host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int groups = kGroups) {
   size_t bytes;
   if (d.prec == PREC_BF16) {
     bytes = tc_smem_bytes(d);
@@ -189,14 +191,15 @@ __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre) {
     bytes = (size_t)pl.end * 4;
   }
   bytes = (bytes + 15) & ~(size_t)15;
-  bytes += sizeof(WarpScratch) * kGroups;
+  bytes += sizeof(WarpScratch) * groups;
   bytes += sizeof(PixSlot) * kTileMax;
-  bytes += sizeof(long long) * 33;
+  bytes += sizeof(long long) * (33 + 16);
   bytes += sizeof(int) * (n_pre + 1 + 4);
   return (bytes + 15) & ~(size_t)15;
 }
 
-__device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, int n_pre) {
+__device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, int n_pre,
+                                          int groups = kGroups) {
   TileSmem t;
   size_t off;
   if (d.prec == PREC_BF16) {
@@ -215,11 +218,13 @@ __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, in
   }
   off = (off + 15) & ~(size_t)15;
   t.ws = reinterpret_cast<WarpScratch*>(smem + off);
-  off += sizeof(WarpScratch) * kGroups;
+  off += sizeof(WarpScratch) * groups;
   t.slots = reinterpret_cast<PixSlot*>(smem + off);
   off += sizeof(PixSlot) * kTileMax;
   t.sh = reinterpret_cast<long long*>(smem + off);
   off += sizeof(long long) * 33;
+  t.pc = reinterpret_cast<long long*>(smem + off);
+  off += sizeof(long long) * 16;
   t.pre = reinterpret_cast<int*>(smem + off);
   t.flag = t.pre + n_pre + 1;
   (void)n_pre;
@@ -240,13 +245,17 @@ __device__ __forceinline__ void load_weights(const DeviceModel& m, TileSmem& t) 
 }
 
 // gather + network for the slots of the tile; P[m][NOp] lands in t.U0.
-template <int PREC, bool kCoherent>
+// With pc non-null (BF16), thread 0 adds its gather cycles to pc[13] and the
+// network's sub-phases to pc[14], pc[15] (shared-memory accumulators).
+template <int PREC, bool kCoherent, int NT = kThreads>
 __device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* units, TileSmem& t,
-                                             int n_valid) {
+                                             int n_valid, long long* pc = nullptr) {
   if constexpr (PREC == PREC_BF16) {
+    const long long c0 = pc != nullptr && threadIdx.x == 0 ? clock64() : 0;
     tc_gather<kCoherent>(units, t.slots, m.d, t.tc, n_valid);
     __syncthreads();
-    tc_network(m.d, t.tc, n_valid);
+    if (pc != nullptr && threadIdx.x == 0) pc[13] += clock64() - c0;
+    tc_network<NT>(m.d, t.tc, n_valid, pc);
   } else {
     gather_f32<kMT, kCoherent>(units, t.slots, m.d.h, t.U0);
     __syncthreads();
