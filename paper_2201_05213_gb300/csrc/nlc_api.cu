@@ -532,8 +532,8 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   if (x->max_ctas > 0) gmax = std::min(gmax, x->max_ctas);
   long long g = (b.max_front + x->px_per_cta - 1) / x->px_per_cta;
   int grid = (int)std::max(1LL, std::min<long long>(g, gmax));
-  // the barrier's arrival counter reaches grid * T; keep it within 32 bits
-  if ((long long)grid * b.T >= (1LL << 32) - 1) grid = 1;
+  // the barrier's arrival counter reaches grid * T; keep it below 2^31 (bit 31 flags a timeout)
+  if ((long long)grid * b.T >= (1LL << 31) - 1) grid = 1;
   const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
   cb.prof = x->d_prof;
   CUDA_TRY(launch_decode(m, cb, d_in, reinterpret_cast<const unsigned long long*>(d_offsets),

@@ -105,39 +105,51 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+
+// Grid-wide barrier of a cooperative launch, split in two so that a CTA can
+// do work that needs no other CTA's results between arriving and waiting.
+// Arrival is a fire-and-forget atomic add to a counter that grows
+// monotonically (generation g completes at nblocks * g arrivals, so it never
+// needs a reset inside the launch); waiters poll the counter.  The wait is
+// bounded: after kSpinLimit polls a CTA records ST_TIMEOUT and sets bit 31
+// of the counter (kBarPoison), which releases every waiting CTA at once and
+// tells it to leave its loop.  Counts stay below 2^31 (the host caps
+// nblocks * steps).
+constexpr unsigned kSpinLimit = 1u << 25;
+constexpr unsigned kBarPoison = 0x80000000u;
+
+// Thread 0, after the CTA's writes (a __syncthreads() must precede).
+__device__ __forceinline__ void grid_arrive(unsigned* count) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);  // result unused: a reduction, no wait for the reply
+  }
 }
 
-// Grid-wide barrier of a cooperative launch.  The arrival counter grows
-// monotonically (generation g completes at nblocks * g arrivals), so it
-// never needs a reset inside the launch.  The wait is bounded: after
-// kSpinLimit polls it records ST_TIMEOUT and returns false, and every CTA
-// then leaves its loop.
-constexpr unsigned kSpinLimit = 1u << 25;
-
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
-                                             unsigned& my_gen, int* status, int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned target = my_gen + 1;
-    __threadfence();
-    unsigned old = atomicAdd(count, 1u);
-    if (old == nblocks * target - 1u) {
-      st_release_gpu(gen, target);
-    } else {
-      unsigned it = 0;
-      while (ld_acquire_gpu(gen) < target) {
-        if (++it > kSpinLimit) {
-          set_status(status, ST_TIMEOUT);
-          *s_flag = 1;
-          break;
-        }
-        __nanosleep(64);
+// Thread 0 waits until nblocks * target CTAs have arrived; then the whole CTA
+// synchronises.  Returns false if the decode must stop (a timeout here or
+// elsewhere).
+__device__ __forceinline__ bool grid_wait(unsigned* count, unsigned nblocks, unsigned target,
+                                          int* status, int* s_flag) {
+  if (threadIdx.x == 0 && *s_flag == 0) {
+    const unsigned goal = nblocks * target;
+    unsigned it = 0;
+    for (;;) {
+      const unsigned c = ld_acquire_gpu(count);
+      if (c & kBarPoison) {
+        *s_flag = 1;
+        break;
       }
+      if (c >= goal) break;
+      if (++it > kSpinLimit) {
+        set_status(status, ST_TIMEOUT);
+        atomicOr(count, kBarPoison);
+        *s_flag = 1;
+        break;
+      }
+      __nanosleep(32);
     }
-    my_gen = target;
-    if (ld_cg_u32((const uint32_t*)status) == ST_TIMEOUT) *s_flag = 1;
+    __threadfence();
   }
   __syncthreads();
   return *s_flag == 0;

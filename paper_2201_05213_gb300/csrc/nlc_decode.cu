@@ -48,7 +48,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
   constexpr int gpw = 32 / GW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / GW, gl = lane % GW;
-  const int K = a.m.d.K, ldP = a.m.d.ldP;
+  const int K = a.m.d.K;
   const bool pr = pc != nullptr && threadIdx.x == 0;
   long long ck = 0;
   auto tick = [&](int slot) {
@@ -78,7 +78,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       ck = clock64();
       pc[12] += 1;
     }
-    comp_init<GW>(t.U0 + (size_t)se * ldP, K, gl, cs);
+    comp_init<GW>(tile_params(t, a.m.d, se), K, gl, cs);
     int v[3] = {0, 0, 0};
     for (int ch = 0; ch < 3; ch++) {
       int nact;
@@ -124,7 +124,6 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   constexpr int MT = tile_size<PREC>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int h = d.h;
-  unsigned my_gen = 0;
   const unsigned G = gridDim.x;
   // phase cycles of thread 0 (shared-memory accumulators): [0] front scan,
   // [1] slot fill, [2] gather + network, [3] per-pixel coding, [4] grid
@@ -139,32 +138,44 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       ck = n_;
     }
   };
+  // slots of the tile of n pixels starting at front position base of step
+  auto fill_slots = [&](int step, long long base, int n) {
+    for (int s = threadIdx.x; s < MT; s += blockDim.x) {
+      PixSlot ps{-1, 0, 0, 0};
+      if (s < n) {
+        const int q = (int)(base + s);
+        int lo2 = 0, hi2 = a.n_units - 1;  // last u with pre[u] <= q
+        while (lo2 < hi2) {
+          int mid = (lo2 + hi2 + 1) >> 1;
+          if (t.pre[mid] <= q) lo2 = mid; else hi2 = mid - 1;
+        }
+        const Unit U = a.units[lo2];
+        const Front fr = unit_front(U, step, h, a.sched);
+        ps.unit = lo2;
+        ps.i = fr.i_lo + (q - t.pre[lo2]);
+        ps.j = front_col(U, step, ps.i, h, a.sched);
+        ps.aux = U.stream_base + (a.layout == 1 ? ps.i : 0);
+      }
+      t.slots[s] = ps;
+    }
+  };
+  // The schedule of step t + 1 (front sizes, this CTA's share, its first
+  // tile's slots) needs no decoded data, so it is computed between arriving
+  // at the grid barrier after step t and waiting for the others.
+  if (pr) ck = clock64();
+  int F = front_scan(a.units, a.n_units, 0, h, a.sched, t.pre, t.sh);
+  tick(0);
+  long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
+  if (lo < hi) fill_slots(0, lo, (int)min((long long)MT, hi - lo));
+  __syncthreads();
+  tick(1);
   for (int step = 0; step < a.T; step++) {
-    if (pr) ck = clock64();
-    const int F = front_scan(a.units, a.n_units, step, h, a.sched, t.pre, t.sh);
-    tick(0);
-    const long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
     for (long long base = lo; base < hi; base += MT) {
       const int n = (int)min((long long)MT, hi - base);
-      for (int s = threadIdx.x; s < MT; s += blockDim.x) {
-        PixSlot ps{-1, 0, 0, 0};
-        if (s < n) {
-          const int q = (int)(base + s);
-          int lo2 = 0, hi2 = a.n_units - 1;  // last u with pre[u] <= q
-          while (lo2 < hi2) {
-            int mid = (lo2 + hi2 + 1) >> 1;
-            if (t.pre[mid] <= q) lo2 = mid; else hi2 = mid - 1;
-          }
-          const Unit U = a.units[lo2];
-          const Front fr = unit_front(U, step, h, a.sched);
-          ps.unit = lo2;
-          ps.i = fr.i_lo + (q - t.pre[lo2]);
-          ps.j = front_col(U, step, ps.i, h, a.sched);
-          ps.aux = U.stream_base + (a.layout == 1 ? ps.i : 0);
-        }
-        t.slots[s] = ps;
+      if (base != lo) {  // further tiles of a large share
+        fill_slots(step, base, n);
+        __syncthreads();
       }
-      __syncthreads();
       // A CTA with at most one pixel per warp codes with whole warps (lower
       // latency per pixel); otherwise two pixels per warp.  Both give the
       // same tables (see cdf_fix).  Lane l of warp w fetches the rANS state
@@ -193,8 +204,17 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       __syncthreads();
       tick(3);
     }
+    if (step + 1 == a.T) break;
+    const unsigned target = (unsigned)step + 1u;
+    if (G > 1) grid_arrive(a.bar);
+    F = front_scan(a.units, a.n_units, step + 1, h, a.sched, t.pre, t.sh);
+    tick(0);
+    lo = (long long)F * blockIdx.x / G;
+    hi = (long long)F * (blockIdx.x + 1) / G;
+    if (lo < hi) fill_slots(step + 1, lo, (int)min((long long)MT, hi - lo));
+    tick(1);
     if (G > 1) {
-      if (!grid_barrier(a.bar, a.bar + 1, G, my_gen, a.status, t.flag)) break;
+      if (!grid_wait(a.bar, G, target, a.status, t.flag)) break;
     } else {
       __syncthreads();
     }

@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   constexpr int MT = tile_size<PREC>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int K = m.d.K, ldP = m.d.ldP;
+  const int K = m.d.K;
   const long long ntiles = (n_px + MT - 1) / MT;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (int s = threadIdx.x; s < MT; s += blockDim.x) {
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const long long q = tile * MT + s;
       WarpScratch& ws = t.ws[2 * warp + half];
       CompState cs;
-      comp_init<kGW>(t.U0 + (size_t)se * ldP, K, gl, cs);
+      comp_init<kGW>(tile_params(t, m.d, se), K, gl, cs);
       for (int ch = 0; ch < 3; ch++) {
         int nact;
         const float mloc = channel_setup<kGW>(cs, K, ch, v[0], v[1], gl, ws, nact);
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   constexpr int MT = tile_size<PREC>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int K = m.d.K, NO = m.d.NO, ldP = m.d.ldP;
+  const int K = m.d.K, NO = m.d.NO;
   const long long ntiles = (n_px + MT - 1) / MT;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (int s = threadIdx.x; s < MT; s += blockDim.x) {
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const Unit U = units[ps.unit];
       // outputs in image raster order
       const long long q = U.img_px_base + (long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j);
-      const float* P = t.U0 + (size_t)s * ldP;
+      const float* P = tile_params(t, m.d, s);
       if (params)
         for (int k = lane; k < NO; k += 32) params[q * NO + k] = P[k];
       if (bits) {

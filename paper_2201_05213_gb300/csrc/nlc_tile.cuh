@@ -181,6 +181,11 @@ struct TileSmem {
   TcSmem tc;
 };
 
+// Network outputs of the tile's m-th pixel.
+__device__ __forceinline__ const float* tile_params(const TileSmem& t, const Dims& d, int m) {
+  return t.U0 + (size_t)m * d.ldP;
+}
+
 // Shared memory of the tile pipeline with `groups` coding groups.
 __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int groups = kGroups) {
   size_t bytes;
