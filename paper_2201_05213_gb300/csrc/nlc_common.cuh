@@ -118,12 +118,12 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 constexpr unsigned kSpinLimit = 1u << 25;
 constexpr unsigned kBarPoison = 0x80000000u;
 
-// Thread 0, after the CTA's writes (a __syncthreads() must precede).
+// Thread 0, after the CTA's writes (a __syncthreads() must precede): a
+// release reduction, cumulative over the CTA's writes that the barrier made
+// visible to thread 0, with no wait for a reply.
 __device__ __forceinline__ void grid_arrive(unsigned* count) {
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);  // result unused: a reduction, no wait for the reply
-  }
+  if (threadIdx.x == 0)
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
 }
 
 // Thread 0 waits until nblocks * target CTAs have arrived; then the whole CTA
@@ -149,7 +149,6 @@ __device__ __forceinline__ bool grid_wait(unsigned* count, unsigned nblocks, uns
       }
       __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();
   return *s_flag == 0;

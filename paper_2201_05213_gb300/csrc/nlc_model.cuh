@@ -404,6 +404,13 @@ __device__ __forceinline__ void comp_init(const float* P, int K, int gl, CompSta
   }
 }
 
+// a[ch] by selects (ch need not be a compile-time constant, so the arrays
+// stay in registers when the channel loop is not unrolled).
+template <class T>
+__device__ __forceinline__ T pick3(const T (&a)[3], int ch) {
+  return ch == 0 ? a[0] : (ch == 1 ? a[1] : a[2]);
+}
+
 // Location of channel ch of component (lane) given decoded r, g.
 __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, int g) {
   const float xr = xval_f(r), xg = xval_f(g);
@@ -440,7 +447,8 @@ __device__ __forceinline__ uint32_t cdf_term(float e, const float4& p) {
 
 // Partial fixed-point F at boundary value e over components i0, i0 + di, ...
 // (di <= 4), four independent terms at a time; entries past the active ones
-// are zero.
+// are zero.  (Handling the remainder exactly instead of padding it measured
+// slower: the larger code costs more than the skipped terms.)
 __device__ __forceinline__ uint32_t cdf_fix(const WarpScratch& ws, int nact, float e, int i0,
                                             int di) {
   uint32_t F = 0;
@@ -492,7 +500,7 @@ __device__ __forceinline__ float channel_setup(const CompState& cs, int K, int c
   nact = __popc(bits);
   for (int p = gl; p < 2 * kMaxK; p += GW)
     if (p >= nact) ws.cp[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (on) ws.cp[__popc(bits & ((1u << gl) - 1u))] = make_float4(m, cs.c[ch], wS, 0.f);
+  if (on) ws.cp[__popc(bits & ((1u << gl) - 1u))] = make_float4(m, pick3(cs.c, ch), wS, 0.f);
   __syncwarp();
   return m;
 }
@@ -562,7 +570,7 @@ __device__ __forceinline__ int table_search(const TableScratch& ws, uint32_t slo
 
 // Posterior update after channel ch took value v (lanes < K).
 __device__ __forceinline__ void comp_observe(CompState& cs, int K, int ch, float m, int v, int gl) {
-  if (gl < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, cs.inv[ch], cs.lme[ch], v));
+  if (gl < K) cs.lw = __fadd_rn(cs.lw, log_bin_mass_f(m, pick3(cs.inv, ch), pick3(cs.lme, ch), v));
 }
 
 }  // namespace nlc
