@@ -334,13 +334,18 @@ __device__ __forceinline__ void tc_issue(const TcSmem& t, uint32_t a_off, uint32
                                          int N) {
   if (threadIdx.x == 0) {
     fence_after_sync();
-    const uint32_t a0 = smem_u32(t.base + a_off), b0 = smem_u32(t.base + b_off);
     const uint32_t sbo = (uint32_t)(Kd / 8) * 128u;
+    const uint64_t da = umma_desc(smem_u32(t.base + a_off), 128u, sbo);
+    const uint64_t db = umma_desc(smem_u32(t.base + b_off), 128u, sbo);
     const uint32_t idesc = idesc_bf16(kTcM, N);
-    for (int s = 0; s < Kd / 16; s++) {
-      mma_bf16(t.tmem, umma_desc(a0 + 256u * s, 128u, sbo), umma_desc(b0 + 256u * s, 128u, sbo),
-               idesc, s > 0 ? 1u : 0u);
-    }
+    const uint32_t tm = t.tmem;
+    // K step s starts 256 bytes further: +16 in the descriptors' address
+    // field (Kd <= 80: at most 5 steps)
+    mma_bf16(tm, da, db, idesc, 0u);
+    if (Kd / 16 > 1) mma_bf16(tm, da + 16, db + 16, idesc, 1u);
+    if (Kd / 16 > 2) mma_bf16(tm, da + 32, db + 32, idesc, 1u);
+    if (Kd / 16 > 3) mma_bf16(tm, da + 48, db + 48, idesc, 1u);
+    if (Kd / 16 > 4) mma_bf16(tm, da + 64, db + 64, idesc, 1u);
     mma_commit(t.mbar);
   }
 }
