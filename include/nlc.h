@@ -136,6 +136,7 @@ int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
 
 /* Decoder phase profile (per-step latency against the dependency-bound step
  * count of Section 3).  enable != 0 makes the following nlc_decompress calls
+ * and nlc_plan_run calls (a captured graph keeps the setting of its capture)
  * record, in thread 0 of every CTA, clock64 cycles spent per phase; a
  * non-NULL h_counters (16 uint64) receives the totals accumulated since the
  * last read, summed over CTAs, and clears them:
@@ -205,6 +206,37 @@ int nlc_compress_noalloc(nlc_ctx* ctx, const nlc_image_in* h_imgs, int n, int pa
 int nlc_decompress(nlc_ctx* ctx, const uint8_t* d_in, const uint64_t* d_offsets,
                    const nlc_image_out* h_outs, int n, int patch, int layout, int schedule,
                    nlc_stream stream);
+
+/* Decode plan: the host side of nlc_decompress for a fixed batch of output
+ * images (unit partition, wavefront schedule of Algorithm 1, device unit
+ * tables, grid size), done once.  nlc_plan_decode allocates the plan's
+ * device buffers and copies its unit tables synchronously; the plan keeps
+ * the output pointers of h_outs (they must stay valid) and uses the
+ * context's weights at run time.  Arguments and errors as nlc_decompress. */
+typedef struct nlc_plan nlc_plan;
+int nlc_plan_decode(nlc_ctx* ctx, const nlc_image_out* h_outs, int n, int patch, int layout,
+                    int schedule, nlc_plan** out);
+
+/* Decodes containers laid out as the plan's images (d_in 16-byte aligned,
+ * d_offsets n+1 device uint64) into the plan's outputs.  Issues device work
+ * only (no allocation, no host copy, no synchronisation), so it may be
+ * captured in a CUDA graph; a graph replay decodes whatever containers are
+ * at d_in then.  Device-side errors go to the context's status word.  Runs
+ * of one plan, and of plans sharing a context, must not overlap. */
+int nlc_plan_run(nlc_plan* plan, const uint8_t* d_in, const uint64_t* d_offsets,
+                 nlc_stream stream);
+
+/* Autotuner of the decoder's front packing: for px_per_cta in 1, 2, 4, ...,
+ * 128 (pixels of each step per CTA, which sets the grid), runs the plan once
+ * to warm up and `reps` times timed with CUDA events, and keeps the fastest
+ * setting in the plan.  Synchronous; decodes (reps + 1) x candidates times.
+ * h_px_per_cta / h_ms (either may be NULL) receive the choice and its time
+ * per decode. */
+int nlc_plan_tune(nlc_plan* plan, const uint8_t* d_in, const uint64_t* d_offsets, int reps,
+                  nlc_stream stream, int* h_px_per_cta, float* h_ms);
+
+/* Frees the plan (synchronises the device). */
+int nlc_plan_destroy(nlc_plan* plan);
 
 /* Network outputs (d_params: sum H W x 10K floats, images in order, pixels
  * in raster order) and/or the model code length -log2 p(x_ij) of every pixel

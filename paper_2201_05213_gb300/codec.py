@@ -67,6 +67,10 @@ class Codec:
             self.check(stream)
         return outs
 
+    def plan(self, sizes, patch=0, layout=1, schedule=N.NLC_SCHED_WAVEFRONT, outs=None):
+        """A DecodePlan for a fixed batch of image sizes."""
+        return DecodePlan(self, sizes, patch, layout, schedule, outs)
+
     def forward(self, imgs, patch=0, params=True, bits=False, stream=None):
         npx = sum(int(t.shape[0]) * int(t.shape[1]) for t in imgs)
         dev = imgs[0].device
@@ -93,6 +97,47 @@ class Codec:
         N.nlc_loss_grad(self.ctx, batch, loss, grad, stream)
         self.check(stream)
         return loss, grad
+
+
+class DecodePlan:
+    """nlc_plan_* for one batch shape: run() issues device work only, so it can
+    be captured with graph(); tune() picks the decoder's pixels per CTA."""
+
+    def __init__(self, codec, sizes, patch, layout, schedule, outs=None):
+        self.codec = codec
+        self.outs = outs if outs is not None else [
+            torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for H, W in sizes]
+        self.handle = N.nlc_plan_decode(codec.ctx, self.outs, patch, layout, schedule)
+
+    def run(self, data, offs, stream=None):
+        N.nlc_plan_run(self.handle, data, offs, stream)
+        return self.outs
+
+    def tune(self, data, offs, reps=2, stream=None):
+        return N.nlc_plan_tune(self.handle, data, offs, reps, stream)
+
+    def graph(self, data, offs):
+        """A torch.cuda.CUDAGraph whose replay decodes the containers at data."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(data, offs, s)  # first run outside the capture
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g):
+            self.run(data, offs, torch.cuda.current_stream())
+        return g
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            N.nlc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class LocalModelNLL(torch.autograd.Function):

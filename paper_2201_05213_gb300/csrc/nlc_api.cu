@@ -57,8 +57,11 @@ struct nlc_ctx {
   size_t ws_cap = 0;
   int px_per_cta = 8;
   int max_ctas = 0;
-  unsigned long long* d_prof = nullptr;  // decoder phase counters while profiling
+  unsigned long long* d_prof = nullptr;  // decoder phase counters (16), allocated once
+  bool prof_on = false;                  // launches receive d_prof only while profiling
 };
+
+static unsigned long long* prof_ptr(const nlc_ctx* x) { return x->prof_on ? x->d_prof : nullptr; }
 
 extern "C" const char* nlc_last_error(void) { return g_err; }
 extern "C" int nlc_abi_version(void) { return NLC_ABI_VERSION; }
@@ -187,6 +190,11 @@ extern "C" int nlc_create(const nlc_model_cfg* cfg, const float* h_w, size_t n, 
     TRY_ALLOC(x->d_v, n * 4);
     TRY_ALLOC(x->d_grad, n * 4);
     TRY_ALLOC(x->d_loss, 8);
+    TRY_ALLOC(x->d_prof, 16 * sizeof(uint64_t));
+    if ((e = cudaMemset(x->d_prof, 0, 16 * sizeof(uint64_t))) != cudaSuccess) {
+      rc = fail(NLC_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
+      break;
+    }
     rc = check_mono(x->device, x->sm_count, reinterpret_cast<unsigned long long*>(x->d_loss));
     if (rc) break;
     if ((e = cudaMemcpy(x->d_w, h_w, n * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -260,24 +268,12 @@ extern "C" int nlc_sync_status(nlc_ctx* x, nlc_stream stream) {
 
 extern "C" int nlc_decode_profile(nlc_ctx* x, int enable, uint64_t* h_counters) {
   if (!x) return fail(NLC_ERR_ARG, "ctx is NULL");
-  if (h_counters) {
-    if (x->d_prof) {
-      CUDA_TRY(cudaDeviceSynchronize());
-      CUDA_TRY(cudaMemcpy(h_counters, x->d_prof, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-      CUDA_TRY(cudaMemset(x->d_prof, 0, 16 * sizeof(uint64_t)));
-    } else {
-      memset(h_counters, 0, 16 * sizeof(uint64_t));
-    }
-  }
-  if (enable && !x->d_prof) {
-    CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMalloc((void**)&x->d_prof, 16 * sizeof(uint64_t)));
+  CUDA_TRY(cudaDeviceSynchronize());
+  if (h_counters)
+    CUDA_TRY(cudaMemcpy(h_counters, x->d_prof, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (h_counters || enable != (int)x->prof_on)
     CUDA_TRY(cudaMemset(x->d_prof, 0, 16 * sizeof(uint64_t)));
-  } else if (!enable && x->d_prof) {
-    CUDA_TRY(cudaDeviceSynchronize());
-    cudaFree(x->d_prof);
-    x->d_prof = nullptr;
-  }
+  x->prof_on = enable != 0;
   return NLC_OK;
 }
 
@@ -535,7 +531,7 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   // the barrier's arrival counter reaches grid * T; keep it below 2^31 (bit 31 flags a timeout)
   if ((long long)grid * b.T >= (1LL << 31) - 1) grid = 1;
   const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
-  cb.prof = x->d_prof;
+  cb.prof = prof_ptr(x);
   CUDA_TRY(launch_decode(m, cb, d_in, reinterpret_cast<const unsigned long long*>(d_offsets),
                          layout, patch, sched, (int)b.T, grid, s));
   return NLC_OK;
@@ -708,5 +704,159 @@ extern "C" int nlc_compress_noalloc(nlc_ctx* x, const nlc_image_in* imgs, int n,
   if ((rc = upload_batch(b, cb, s))) return rc;
   CUDA_TRY(launch_encode(model_view(x), cb, layout, patch, d_out, (unsigned long long)cap,
                          reinterpret_cast<unsigned long long*>(d_offsets), x->sm_count, s));
+  return NLC_OK;
+}
+
+// ---------------------------------------------------------------------
+// Decode plans: the host work of nlc_decompress (unit partition, schedule,
+// device unit tables, grid size) done once, so that a run issues device work
+// only and can be captured in a CUDA graph; plus a tuner of the decoder's
+// pixels per CTA and step.
+// ---------------------------------------------------------------------
+struct nlc_plan {
+  nlc_ctx* x = nullptr;
+  int n = 0, patch = 0, layout = 0, sched = 0;
+  long long T = 0, max_front = 0;
+  int n_units = 0, grid = 1, gmax = 1, px_per_cta = 8;
+  unsigned char* d_buf = nullptr;
+  CodecBufs cb;
+};
+
+static int plan_grid(const nlc_plan* p, int px_per_cta) {
+  long long g = (p->max_front + px_per_cta - 1) / px_per_cta;
+  int grid = (int)std::max(1LL, std::min<long long>(g, p->gmax));
+  if ((long long)grid * p->T >= (1LL << 31) - 1) grid = 1;
+  return grid;
+}
+
+extern "C" int nlc_plan_decode(nlc_ctx* x, const nlc_image_out* outs, int n, int patch,
+                               int layout, int schedule, nlc_plan** out) {
+  if (!out) return fail(NLC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!x || (n > 0 && !outs) || n < 0 || (layout != 0 && layout != 1))
+    return fail(NLC_ERR_ARG, "bad arguments");
+  if (schedule < 0 || schedule > 2) return fail(NLC_ERR_ARG, "unknown schedule %d", schedule);
+  if (layout == NLC_LAYOUT_UNIT && schedule == NLC_SCHED_WAVEFRONT)
+    return fail(NLC_ERR_ARG, "one stream per unit can only be decoded in raster order");
+  std::vector<int32_t> H(n), W(n);
+  std::vector<const void*> data(n);
+  std::vector<uint8_t*> ptrs(n);
+  for (int i = 0; i < n; i++) {
+    H[i] = outs[i].H;
+    W[i] = outs[i].W;
+    data[i] = outs[i].data;
+    ptrs[i] = outs[i].data;
+  }
+  int rc = check_images(n, H.data(), W.data(), data.data(), patch);
+  if (rc) return rc;
+  Batch b;
+  rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, layout, schedule, b);
+  if (rc) return rc;
+  if (decode_smem_bytes(x->d, (int)b.units.size()) > 227 * 1024)
+    return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
+  nlc_plan* p = new nlc_plan();
+  p->x = x;
+  p->n = n;
+  p->patch = patch;
+  p->layout = layout;
+  p->sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
+  p->T = b.T;
+  p->max_front = b.max_front;
+  p->n_units = (int)b.units.size();
+  p->px_per_cta = x->px_per_cta;
+  const size_t need = layout_bufs(b, nullptr, p->cb, x->d_status, false);
+  cudaError_t e = cudaMalloc((void**)&p->d_buf, std::max<size_t>(need, 256));
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(NLC_ERR_CUDA, "cudaMalloc failed: %s", cudaGetErrorString(e));
+  }
+  layout_bufs(b, p->d_buf, p->cb, x->d_status, false);
+  if (!b.units.empty())
+    e = cudaMemcpy((void*)p->cb.units, b.units.data(), b.units.size() * sizeof(Unit),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !b.images.empty())
+    e = cudaMemcpy((void*)p->cb.images, b.images.data(), b.images.size() * sizeof(ImageRec),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p->d_buf);
+    delete p;
+    return fail(NLC_ERR_CUDA, "unit table upload failed: %s", cudaGetErrorString(e));
+  }
+  // sets the decoder's shared-memory attribute for this batch, so runs need not
+  p->gmax = decode_max_grid(model_view(x), p->n_units, x->sm_count);
+  if (p->gmax < 1) {
+    cudaFree(p->d_buf);
+    delete p;
+    return fail(NLC_ERR_UNSUPPORTED, "decoder does not fit on an SM");
+  }
+  if (x->max_ctas > 0) p->gmax = std::min(p->gmax, x->max_ctas);
+  p->grid = plan_grid(p, p->px_per_cta);
+  *out = p;
+  return NLC_OK;
+}
+
+extern "C" int nlc_plan_run(nlc_plan* p, const uint8_t* d_in, const uint64_t* d_offsets,
+                            nlc_stream stream) {
+  if (!p || (p->n > 0 && (!d_in || !d_offsets))) return fail(NLC_ERR_ARG, "bad arguments");
+  if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(NLC_ERR_ARG, "d_in must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_packed(p->x, s);
+  if (rc) return rc;
+  p->cb.prof = prof_ptr(p->x);  // as of this call (a captured graph keeps it)
+  CUDA_TRY(launch_decode(model_view(p->x), p->cb, d_in,
+                         reinterpret_cast<const unsigned long long*>(d_offsets), p->layout,
+                         p->patch, p->sched, (int)p->T, p->grid, s, false));
+  return NLC_OK;
+}
+
+extern "C" int nlc_plan_tune(nlc_plan* p, const uint8_t* d_in, const uint64_t* d_offsets,
+                             int reps, nlc_stream stream, int* h_px_per_cta, float* h_ms) {
+  if (!p || reps < 1) return fail(NLC_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  static const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_ppc = p->px_per_cta, best_grid = p->grid, last_grid = -1, rc = NLC_OK;
+  for (int c : cand) {
+    const int grid = plan_grid(p, c);
+    if (grid == last_grid) continue;  // same launch as the previous candidate
+    last_grid = grid;
+    p->grid = grid;
+    if ((rc = nlc_plan_run(p, d_in, d_offsets, stream))) break;  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && rc == NLC_OK; r++) rc = nlc_plan_run(p, d_in, d_offsets, stream);
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = fail(NLC_ERR_CUDA, "tuning run failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (best == 0.f || ms < best) {
+      best = ms;
+      best_ppc = c;
+      best_grid = grid;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->grid = best_grid;
+  p->px_per_cta = best_ppc;
+  if (rc) return rc;
+  if (h_px_per_cta) *h_px_per_cta = best_ppc;
+  if (h_ms) *h_ms = best;
+  return NLC_OK;
+}
+
+extern "C" int nlc_plan_destroy(nlc_plan* p) {
+  if (!p) return NLC_OK;
+  cudaDeviceSynchronize();
+  cudaFree(p->d_buf);
+  delete p;
   return NLC_OK;
 }

@@ -257,7 +257,7 @@ int decode_max_grid(const DeviceModel& m, int n_units, int sm_count) {
 
 cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
                           const unsigned long long* d_offsets, int layout, int patch, int sched,
-                          int T, int grid, cudaStream_t s) {
+                          int T, int grid, cudaStream_t s, bool set_attr) {
   cudaError_t e;
   if (b.n_images == 0) return cudaSuccess;
   if ((e = launch_parse(m, b, in, d_offsets, layout, patch, s)) != cudaSuccess) return e;
@@ -280,8 +280,9 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
   const void* fn = decode_fn(m.d.prec);
   const int nt = decode_threads_of(m.d.prec);
-  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
+  if (set_attr &&
+      (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess)
     return e;
   void* args[] = {&a};
   if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(nt), args, smem, s);

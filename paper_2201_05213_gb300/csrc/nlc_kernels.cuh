@@ -62,9 +62,11 @@ cudaError_t launch_enc_tables(const DeviceModel& m, const CodecBufs& b, int sm_c
 cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
                          const unsigned long long* d_offsets, int layout, int patch,
                          cudaStream_t s);
+// set_attr = false skips cudaFuncSetAttribute (already set by decode_max_grid
+// for the same batch), so that the call issues device work only.
 cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
                           const unsigned long long* d_offsets, int layout, int patch, int sched,
-                          int T, int grid, cudaStream_t s);
+                          int T, int grid, cudaStream_t s, bool set_attr = true);
 int decode_max_grid(const DeviceModel& m, int n_units, int sm_count);
 size_t decode_smem_bytes(const Dims& d, int n_units);
 cudaError_t launch_forward(const DeviceModel& m, const CodecBufs& b, float* params, float* bits,

@@ -38,6 +38,7 @@ EXPORTS = [
     "nlc_compress_bound", "nlc_compress", "nlc_decompress", "nlc_forward", "nlc_tables",
     "nlc_rans_encode", "nlc_rans_decode", "nlc_train_step", "nlc_loss_grad",
     "nlc_compress_noalloc", "nlc_decode_profile",
+    "nlc_plan_decode", "nlc_plan_run", "nlc_plan_tune", "nlc_plan_destroy",
 ]
 
 
@@ -91,6 +92,10 @@ def load():
             L.nlc_loss_grad.argtypes = [p, p, i, i, i, p, p, p]
             L.nlc_compress_noalloc.argtypes = [p, p, i, i, i, p, sz, p, p]
             L.nlc_decode_profile.argtypes = [p, i, p]
+            L.nlc_plan_decode.argtypes = [p, p, i, i, i, i, p]
+            L.nlc_plan_run.argtypes = [p, p, p, p]
+            L.nlc_plan_tune.argtypes = [p, p, p, i, p, p, p]
+            L.nlc_plan_destroy.argtypes = [p]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -219,6 +224,31 @@ def nlc_decompress(ctx, data, offsets, outs, patch, layout, schedule, stream=Non
     arr = _images(outs)
     return _check(load().nlc_decompress(ctx, _ptr(data), _ptr(offsets), arr, len(outs), patch,
                                         layout, schedule, _stream(stream)))
+
+
+def nlc_plan_decode(ctx, outs, patch, layout, schedule):
+    """Plan for decoding into the (H, W, 3) uint8 CUDA tensors outs (kept by
+    the caller for the plan's lifetime)."""
+    arr = _images(outs)
+    plan = C.c_void_p()
+    _check(load().nlc_plan_decode(ctx, arr, len(outs), patch, layout, schedule, C.byref(plan)))
+    return plan
+
+
+def nlc_plan_run(plan, data, offsets, stream=None):
+    return _check(load().nlc_plan_run(plan, _ptr(data), _ptr(offsets), _stream(stream)))
+
+
+def nlc_plan_tune(plan, data, offsets, reps=2, stream=None):
+    """Returns (px_per_cta, ms per decode) of the fastest setting."""
+    ppc, ms = C.c_int(0), C.c_float(0)
+    _check(load().nlc_plan_tune(plan, _ptr(data), _ptr(offsets), int(reps), _stream(stream),
+                                C.byref(ppc), C.byref(ms)))
+    return ppc.value, ms.value
+
+
+def nlc_plan_destroy(plan):
+    return _check(load().nlc_plan_destroy(plan))
 
 
 def nlc_forward(ctx, imgs, patch, params=None, bits=None, stream=None):

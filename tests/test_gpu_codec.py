@@ -209,3 +209,40 @@ def test_streams_equal_oracle_rans_on_gpu_tables(prec):
 def _check_increasing(cum):
     assert (cum[..., 0] == 0).all() and (cum[..., 256] == 65536).all()
     assert (np.diff(cum, axis=-1) >= 1).all()
+
+
+def test_plan_graph_replay_and_tuner():
+    # a decode plan issues device work only: it runs, tunes its pixels per CTA,
+    # and its CUDA-graph capture decodes whatever containers are in the
+    # captured buffers at replay time
+    codec, _ = make_codec((3, 64, 2, 10), N.NLC_BF16, seed=1)
+    sizes = [(96, 80), (64, 64), (33, 47)]
+    imgs = images(21, sizes)
+    data, offs = codec.compress([to_dev(i) for i in imgs], 32, 1)
+    plan = codec.plan(sizes, 32, 1)
+    outs = plan.run(data, offs)
+    codec.check()
+    for o, i in zip(outs, imgs):
+        assert np.array_equal(o.cpu().numpy(), i)
+    ppc, ms = plan.tune(data, offs, reps=1)
+    assert ppc in (1, 2, 4, 8, 16, 32, 64, 128) and ms > 0
+    codec.check()
+    g = plan.graph(data, offs)
+    for o in plan.outs:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    codec.check()
+    for o, i in zip(plan.outs, imgs):
+        assert np.array_equal(o.cpu().numpy(), i)
+    imgs2 = images(22, sizes)
+    data2, offs2 = codec.compress([to_dev(i) for i in imgs2], 32, 1)
+    assert data2.numel() == data.numel()
+    data.copy_(data2)
+    offs.copy_(offs2)
+    g.replay()
+    torch.cuda.synchronize()
+    codec.check()
+    for o, i in zip(plan.outs, imgs2):
+        assert np.array_equal(o.cpu().numpy(), i)
+    plan.close()
