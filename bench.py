@@ -227,6 +227,8 @@ def main():
     ap.add_argument("--no-seq", action="store_true", help="skip the sequential baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
+    ap.add_argument("--max-ctas", type=int, default=0,
+                    help="cap the decoder's CTAs (0 = all co-resident; profiling of small cases)")
     args = ap.parse_args()
     global SIZES
     SIZES = WORKLOADS[args.workload]
@@ -255,6 +257,8 @@ def main():
     n_px = sum(h * w for h, w in SIZES)
     w0 = synth.xavier_weights(*CFG, seed=0)
     codec = CD.Codec(*CFG, N.NLC_BF16, w0)
+    if args.max_ctas > 0:
+        N.nlc_set_tuning(codec.ctx, 8, args.max_ctas)
     t0 = time.perf_counter()
     train_loss = train_model(codec, args.train_steps) if args.train_steps > 0 else None
     torch.cuda.synchronize()

@@ -414,8 +414,7 @@ static size_t layout_bufs(const Batch& b, unsigned char* base, CodecBufs& cb, in
   cb.unit_bytes = a.take<unsigned long long>(U + 1 + (b.images.size() + 1) / 2 + 1);
   cb.unit_off = a.take<unsigned long long>(U + 1);
   cb.st_pos = a.take<unsigned long long>(S + 1);
-  cb.st_x = a.take<uint32_t>(S + 1);
-  cb.st_end = a.take<unsigned long long>(S + 1);
+  cb.st = a.take<StreamRec>(S + 1);
   cb.bar = a.take<unsigned>(64);
   if (encode) {
     cb.stage = a.take<uint32_t>(3 * (size_t)b.n_px + 1);

@@ -420,9 +420,8 @@ __global__ void parse_streams_kernel(const Unit* __restrict__ units, int n_units
                                      const uint8_t* __restrict__ in,
                                      const int32_t* __restrict__ lens,
                                      const unsigned long long* __restrict__ unit_off,
-                                     const int* __restrict__ bad, uint32_t* __restrict__ st_x,
-                                     unsigned long long* __restrict__ st_pos,
-                                     unsigned long long* __restrict__ st_end, int* status) {
+                                     const int* __restrict__ bad, StreamRec* __restrict__ st,
+                                     int* status) {
   __shared__ long long sh[33];
   const int u = blockIdx.x;
   if (u >= n_units) return;
@@ -443,16 +442,26 @@ __global__ void parse_streams_kernel(const Unit* __restrict__ units, int n_units
         x = ((uint32_t)in[p] << 24) | ((uint32_t)in[p + 1] << 16) | ((uint32_t)in[p + 2] << 8) |
             (uint32_t)in[p + 3];
       }
+      StreamRec r;
+      r.pad = 0;
       if (!ok || len < 4 || x < kRansL || x >= (1u << 31)) {
         if (ok) set_status(status, ST_CORRUPT);
-        st_x[s] = kRansL;
-        st_pos[s] = p;
-        st_end[s] = p;
+        r.x = kRansL;
+        r.pos = r.end = p;
       } else {
-        st_x[s] = x;
-        st_pos[s] = p + 4;
-        st_end[s] = p + (unsigned long long)len;
+        r.x = x;
+        r.pos = p + 4;
+        r.end = p + (unsigned long long)len;
       }
+      // the stream's first 8 payload bytes (0 past its end)
+      uint32_t w[2] = {0u, 0u};
+      for (int q = 0; q < 8; q++) {
+        const unsigned long long pq = r.pos + (unsigned long long)q;
+        if (pq < r.end) w[q >> 2] |= (uint32_t)in[pq] << (8 * (q & 3));
+      }
+      r.b0 = w[0];
+      r.b1 = w[1];
+      st[s] = r;
     }
     run += total;
   }
@@ -474,7 +483,7 @@ cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t
                                      bad, b.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   parse_streams_kernel<<<b.n_units, 256, 0, s>>>(b.units, b.n_units, layout, in, b.lens,
-                                                 b.unit_off, bad, b.st_x, b.st_pos, b.st_end,
+                                                 b.unit_off, bad, b.st,
                                                  b.status);
   return cudaGetLastError();
 }

@@ -17,9 +17,7 @@ struct DecodeArgs {
   int n_units;
   int layout, sched, T;
   const uint8_t* in;
-  uint32_t* st_x;
-  unsigned long long* st_pos;
-  const unsigned long long* st_end;
+  StreamRec* st;
   unsigned* bar;
   int* status;
   unsigned long long* prof;  // optional per-phase cycle counters
@@ -69,6 +67,8 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
     dec.end = __shfl_sync(0xffffffffu, pd.end, src);
     dec.lo = __shfl_sync(0xffffffffu, pd.lo, src);
     dec.hi = __shfl_sync(0xffffffffu, pd.hi, src);
+    dec.w2 = __shfl_sync(0xffffffffu, pd.w2, src);
+    dec.w3 = __shfl_sync(0xffffffffu, pd.w3, src);
     dec.used = 0;
     dec.bad = false;
     const PixSlot ps = t.slots[se];
@@ -102,8 +102,11 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       px[2] = (uint8_t)v[2];
       const int sid = ps.aux;
       const unsigned long long np = dec.pos + (unsigned long long)dec.used;
-      a.st_x[sid] = dec.x;
-      a.st_pos[sid] = np;
+      uint32_t n0, n1;
+      dec.next_bytes(n0, n1);
+      StreamRec* r = a.st + sid;
+      *reinterpret_cast<uint4*>(r) = make_uint4(dec.x, n0, n1, 0u);
+      r->pos = np;
       const bool last = a.layout == 1 ? (ps.j == U.Wu - 1) : (ps.i == U.Hu - 1 && ps.j == U.Wu - 1);
       if (dec.bad || (last && (dec.x != kRansL || np != dec.end))) set_status(a.status, ST_CORRUPT);
     }
@@ -184,15 +187,21 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       GroupRansDec pd;
       pd.x = 0;
       pd.pos = pd.end = 0;
-      pd.lo = pd.hi = 0;
+      pd.lo = pd.hi = pd.w2 = pd.w3 = 0;
       {
         const int sl = wide ? group_slot<32, NW>(warp, lane) : group_slot<kGW, NW>(warp, lane);
         if (sl < n) {
-          const int sid = t.slots[sl].aux;
-          pd.x = ld_cg_u32(a.st_x + sid);
-          pd.pos = ld_cg_u64(a.st_pos + sid);
-          pd.end = a.st_end[sid];
-          pd.load_bytes(a.in);
+          // the stream's record in one round trip; the window after its 8
+          // bytes is needed only when the pixel is done
+          const StreamRec* r = a.st + t.slots[sl].aux;
+          const uint4 q = ld_cg_v4(reinterpret_cast<const uint4*>(r));
+          const ulonglong2 pe = ld_cg_v2_u64(&r->pos);
+          pd.x = q.x;
+          pd.lo = q.y;
+          pd.hi = q.z;
+          pd.pos = pe.x;
+          pd.end = pe.y;
+          pd.load_window(a.in);
         }
       }
       if (pr) pc[5] += 1;
@@ -271,9 +280,7 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   a.sched = sched;
   a.T = T;
   a.in = in;
-  a.st_x = b.st_x;
-  a.st_pos = b.st_pos;
-  a.st_end = b.st_end;
+  a.st = b.st;
   a.bar = b.bar;
   a.status = b.status;
   a.prof = b.prof;

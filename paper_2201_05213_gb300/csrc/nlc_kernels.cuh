@@ -29,6 +29,16 @@ struct DeviceModel {
   const unsigned long long* hash;
 };
 
+// Decoder state of one rANS stream between wavefront steps: state x, the
+// next 8 stream bytes (b0 = bytes pos .. pos+3, little-endian; b1 = pos+4 ..
+// pos+7; bytes at or past `end` are unspecified and never consumed by a
+// valid stream), the read position and the end (absolute offsets into the
+// batch of containers).  Loaded with two 16-byte loads.
+struct alignas(16) StreamRec {
+  uint32_t x, b0, b1, pad;
+  unsigned long long pos, end;
+};
+
 // Per-call device buffers (sub-allocated from the context workspace).
 struct CodecBufs {
   const Unit* units;
@@ -41,10 +51,10 @@ struct CodecBufs {
   int32_t* lens;                 // n_streams
   unsigned long long* unit_bytes;  // n_units
   unsigned long long* unit_off;    // n_units (absolute byte offset of the unit's first stream)
-  // decoder
-  uint32_t* st_x;
+  // encoder scratch (u64 per stream)
   unsigned long long* st_pos;
-  unsigned long long* st_end;
+  // decoder
+  StreamRec* st;
   unsigned* bar;                 // 2 words: arrivals, generation
   int* status;
   unsigned long long* prof = nullptr;  // decoder phase cycle counters (8), optional

@@ -277,6 +277,7 @@ __device__ __forceinline__ float log_bin_mass_f(float m, float inv, float lme, i
 // loops may read past the last active component.
 struct alignas(16) WarpScratch {
   float4 cp[2 * kMaxK];
+  float4 pad;  // 528-byte stride: the two groups of a warp read different banks
 };
 
 // Table of one coding warp for decoding with an explicit cum[0..255]

@@ -97,14 +97,44 @@ constexpr int kGW = 16;
 constexpr int kGroups = kThreads / kGW;
 
 // Decoder of one rANS stream position, held uniformly by a coding group.
-// The next 8 stream bytes (a pixel consumes at most 6) are prefetched into
-// two registers.
+// The next 8 stream bytes (a pixel consumes at most 6) are held in two
+// registers; w2, w3 hold the 8 after them, from which the state written back
+// for the stream's next pixel takes its 8 bytes.
 struct GroupRansDec {
   uint32_t x;
   unsigned long long pos, end;
   uint32_t lo, hi;  // bytes pos .. pos+7, little-endian packed
+  uint32_t w2, w3;  // bytes pos+8 .. pos+15
   int used;
   bool bad;
+
+  // w2, w3 from the stream at base: aligned words that hold a byte before
+  // `end` only (so no word outside the stream's container is read).
+  __device__ __forceinline__ void load_window(const uint8_t* base) {
+    const unsigned long long a = pos + 8;
+    const unsigned long long w0 = a & ~3ull;
+    uint32_t v[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const unsigned long long wa = w0 + 4ull * q;
+      v[q] = wa < end ? *reinterpret_cast<const uint32_t*>(base + wa) : 0u;
+    }
+    const uint32_t sh = 8u * (uint32_t)(a & 3ull);
+    w2 = __funnelshift_r(v[0], v[1], sh);
+    w3 = __funnelshift_r(v[1], v[2], sh);
+  }
+  // The 8 bytes at pos + used (used <= 6 for a valid pixel).
+  __device__ __forceinline__ void next_bytes(uint32_t& n0, uint32_t& n1) const {
+    if (used < 4) {
+      const uint32_t s = 8u * (uint32_t)used;
+      n0 = __funnelshift_r(lo, hi, s);
+      n1 = __funnelshift_r(hi, w2, s);
+    } else {
+      const uint32_t s = 8u * (uint32_t)(used - 4);
+      n0 = __funnelshift_r(hi, w2, s);
+      n1 = __funnelshift_r(w2, w3, s);
+    }
+  }
 
   __device__ __forceinline__ void load_bytes(const uint8_t* base) {
     lo = hi = 0;
