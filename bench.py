@@ -151,7 +151,7 @@ def train_model(codec, steps, batch=64, lr=2e-3, seed=1):
     return last
 
 
-def oracle_sample_bpd(w, imgs, n=256, seed=0):
+def oracle_sample_bpd(w, imgs, n=256, seed=0, patch=PATCH):
     """FP64 oracle model code length (bits/dim) of n sampled pixels, patch units."""
     import oracle as O
     rng = np.random.default_rng(seed)
@@ -161,11 +161,76 @@ def oracle_sample_bpd(w, imgs, n=256, seed=0):
         i = int(rng.integers(0, len(imgs)))
         H, W = imgs[i].shape[:2]
         y, x = int(rng.integers(0, H)), int(rng.integers(0, W))
-        P = O.forward_pixels(CFG, w, imgs[i], [y], [x], patch=PATCH)[0]
+        P = O.forward_pixels(CFG, w, imgs[i], [y], [x], patch=patch)[0]
         b = O.pixel_bits(CFG[3], P, *imgs[i][y, x])
         per.append((i, y, x, b))
         tot += b
     return tot / (3 * n), per
+
+
+def uneven_batch_report(codec, w, stream, reps=5):
+    """256 generator images with sides uniform in {32, 48, ..., 512} (seed 3),
+    whole images as units, one stream per row: one tuned decode plan replayed
+    from a CUDA graph; per-image decode latency from the decoder's step end
+    times (image i ends at step W_i + (H_i - 1)(h + 1), Algorithm 1)."""
+    import torch
+    from paper_2201_05213_gb300 import nlc as N
+    from paper_2201_05213_gb300 import synth
+    sizes = synth.uneven_sizes(3, 256)
+    imgs = synth.make_batch(3, sizes)
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    n_px = sum(H * W for H, W in sizes)
+    data, offs = codec.compress(d, 0, N.NLC_LAYOUT_ROW)
+    plan = codec.plan(sizes, 0, N.NLC_LAYOUT_ROW)
+    ppc, _ = plan.tune(data, offs, reps=1, stream=stream)
+    graph = plan.graph(data, offs)
+    for _ in range(2):
+        graph.replay()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    codec.check()
+    for o, i in zip(plan.outs, imgs):
+        assert np.array_equal(o.cpu().numpy(), i), "uneven batch round trip differs"
+    h = CFG[0]
+    steps = np.array([W + (H - 1) * (h + 1) for H, W in sizes])
+    times = torch.zeros(int(steps.max()) + 1, dtype=torch.int64, device="cuda")
+    N.nlc_decode_step_times(codec.ctx, times)
+    plan.run(data, offs, stream)
+    torch.cuda.synchronize()
+    N.nlc_decode_step_times(codec.ctx, None)
+    t = times.cpu().numpy()
+    lat = (t[steps] - t[0]) / 1e6
+    _, bits = codec.forward(d, 0, params=False, bits=True)
+    ob, per = oracle_sample_bpd(w, imgs, n=128, seed=1, patch=0)
+    base = np.cumsum([0] + [H * W for H, W in sizes])
+    bits_np = bits.cpu().numpy()
+    gb = sum(float(bits_np[base[i] + y * sizes[i][1] + x]) for i, y, x, _ in per) / (3 * len(per))
+    plan.close()
+    return {"workload": "256 images, sides uniform in {32,48,...,512} (seed 3), whole images, "
+                        "row streams, h=3 C=64 R=2 K=10 BF16",
+            "pixels": n_px, "value": n_px / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "px_per_cta": ppc, "steps": int(steps.max()),
+            "image_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                 "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "bpd": {"actual": 8.0 * int(offs[-1]) / (3 * n_px),
+                    "gpu_model": float(bits.double().sum()) / (3 * n_px),
+                    "oracle_model_sample": ob, "gpu_model_sample": gb,
+                    "sample": "128 random pixels"}}
+
+
+def heldout_bpd(codec, n=256, seed=5):
+    """Model code length of n held-out 32x32 generator images (bits/dim)."""
+    import torch
+    from paper_2201_05213_gb300 import synth
+    d = [torch.from_numpy(i).cuda() for i in synth.make_batch(seed, [(32, 32)] * n)]
+    _, bits = codec.forward(d, 0, params=False, bits=True)
+    return float(bits.double().sum()) / (3 * 32 * 32 * n)
 
 
 def cpu_baseline(w, img, budget_s=12.0):
@@ -227,6 +292,7 @@ def main():
     ap.add_argument("--no-seq", action="store_true", help="skip the sequential baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-uneven", action="store_true", help="skip the 256-image uneven batch")
     ap.add_argument("--max-ctas", type=int, default=0,
                     help="cap the decoder's CTAs (0 = all co-resident; profiling of small cases)")
     args = ap.parse_args()
@@ -427,7 +493,13 @@ def main():
                         "oracle_model_sample": oracle_bpd, "gpu_model_sample": gsum / (3 * 192),
                         "sample": "192 random pixels"}
         extra["encode"] = {"value": n_px / (enc_ms / 1e3), "unit": "encoded px/s", "ms": enc_ms}
-        extra["train"] = {"steps": args.train_steps, "seconds": train_s, "final_loss_bpd": train_loss}
+        extra["train"] = {"steps": args.train_steps, "batch": 64, "crop": "32x32",
+                          "seconds": train_s, "steps_per_s": args.train_steps / max(train_s, 1e-9),
+                          "final_loss_bpd": train_loss,
+                          "heldout_bpd": heldout_bpd(codec),
+                          "heldout": "256 generator images of 32x32 (seed 5)"}
+        if not args.no_uneven:
+            extra["uneven_batch"] = uneven_batch_report(codec, w.astype(np.float64), stream)
 
     peaks, src = _measured_peaks()
     # roofline of the decode kernel: MUFU work of the symbol search, two

@@ -151,6 +151,19 @@ int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
  * Synchronises the device when reading or changing the mode. */
 int nlc_decode_profile(nlc_ctx* ctx, int enable, uint64_t* h_counters);
 
+/* Step end times of the following nlc_decompress and nlc_plan_run calls (a
+ * captured graph keeps the buffer of its capture): the decoder zeroes
+ * d_times[0 .. n) and writes, in %globaltimer nanoseconds, d_times[0] = its
+ * start and d_times[t + 1] = the time at which every CTA has finished
+ * wavefront step t (the release of the grid barrier after it; the last step:
+ * the latest CTA end), for the entries below n.  With the unit partition and
+ * Algorithm 1's step count W_u + (H_u - 1)(h + 1) of each unit (all units
+ * start at step 0 under the wavefront schedule), an image's decode latency
+ * in a batch is d_times[T_i] - d_times[0], T_i its units' largest step
+ * count.  d_times = NULL (n = 0) stops the stamping; the caller owns the
+ * buffer, which must outlive the calls that use it. */
+int nlc_decode_step_times(nlc_ctx* ctx, uint64_t* d_times, int64_t n);
+
 /* Upper bound of the compressed size of n images with the given sizes, unit
  * partition and layout: per image 32 + 4 n_streams + 6 H W + 4 n_streams
  * bytes, rounded up to 16.  `patch` = side of the square coding units (0 =

@@ -59,6 +59,8 @@ struct nlc_ctx {
   int max_ctas = 0;
   unsigned long long* d_prof = nullptr;  // decoder phase counters (16), allocated once
   bool prof_on = false;                  // launches receive d_prof only while profiling
+  unsigned long long* d_times = nullptr;  // caller's buffer of decoder step end times
+  long long n_times = 0;
 };
 
 static unsigned long long* prof_ptr(const nlc_ctx* x) { return x->prof_on ? x->d_prof : nullptr; }
@@ -264,6 +266,14 @@ extern "C" int nlc_sync_status(nlc_ctx* x, nlc_stream stream) {
     case ST_TIMEOUT: return fail(NLC_ERR_TIMEOUT, "a bounded device wait timed out");
     default: return fail(st, "device status %d", st);
   }
+}
+
+extern "C" int nlc_decode_step_times(nlc_ctx* x, uint64_t* d_times, int64_t n) {
+  if (!x || n < 0 || (n > 0 && !d_times)) return fail(NLC_ERR_ARG, "bad arguments");
+  if (reinterpret_cast<uintptr_t>(d_times) % 8) return fail(NLC_ERR_ARG, "d_times must be 8-byte aligned");
+  x->d_times = n > 0 ? reinterpret_cast<unsigned long long*>(d_times) : nullptr;
+  x->n_times = n;
+  return NLC_OK;
 }
 
 extern "C" int nlc_decode_profile(nlc_ctx* x, int enable, uint64_t* h_counters) {
@@ -531,6 +541,8 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   if ((long long)grid * b.T >= (1LL << 31) - 1) grid = 1;
   const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
   cb.prof = prof_ptr(x);
+  cb.times = x->d_times;
+  cb.n_times = x->n_times;
   CUDA_TRY(launch_decode(m, cb, d_in, reinterpret_cast<const unsigned long long*>(d_offsets),
                          layout, patch, sched, (int)b.T, grid, s));
   return NLC_OK;
@@ -802,6 +814,8 @@ extern "C" int nlc_plan_run(nlc_plan* p, const uint8_t* d_in, const uint64_t* d_
   int rc = ensure_packed(p->x, s);
   if (rc) return rc;
   p->cb.prof = prof_ptr(p->x);  // as of this call (a captured graph keeps it)
+  p->cb.times = p->x->d_times;
+  p->cb.n_times = p->x->n_times;
   CUDA_TRY(launch_decode(model_view(p->x), p->cb, d_in,
                          reinterpret_cast<const unsigned long long*>(d_offsets), p->layout,
                          p->patch, p->sched, (int)p->T, p->grid, s, false));

@@ -21,6 +21,8 @@ struct DecodeArgs {
   unsigned* bar;
   int* status;
   unsigned long long* prof;  // optional per-phase cycle counters
+  unsigned long long* times;  // optional: [0] start, [t + 1] end of step t (ns)
+  long long n_times;
 };
 
 // Threads of the decoder's CTA: the BF16 pipeline runs 16 warps (32 coding
@@ -124,6 +126,10 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   if (threadIdx.x == 0) t.flag[0] = 0;
   if (threadIdx.x < 16) t.pc[threadIdx.x] = 0;
   __syncthreads();
+  // step end times: CTA 0 stamps each step when the grid barrier after it
+  // releases (every CTA has finished it); every CTA stamps the last step's end
+  const bool stamp = a.times != nullptr && threadIdx.x == 0;
+  if (stamp && blockIdx.x == 0 && a.n_times > 0) a.times[0] = global_ns();
   constexpr int MT = tile_size<PREC>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int h = d.h;
@@ -228,7 +234,9 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       __syncthreads();
     }
     tick(4);
+    if (stamp && blockIdx.x == 0 && step + 1 < a.n_times) a.times[step + 1] = global_ns();
   }
+  if (stamp && a.T < a.n_times) atomicMax(a.times + a.T, global_ns());
   if (pr) {
     for (int i = 0; i < 16; i++)
       if (i != 6 && i != 7) atomicAdd(a.prof + i, (unsigned long long)pc[i]);
@@ -272,6 +280,10 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   if ((e = launch_parse(m, b, in, d_offsets, layout, patch, s)) != cudaSuccess) return e;
   if (b.n_units == 0) return cudaSuccess;
   if ((e = cudaMemsetAsync(b.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+  if (b.times != nullptr && b.n_times > 0 &&
+      (e = cudaMemsetAsync(b.times, 0, (size_t)b.n_times * sizeof(unsigned long long), s)) !=
+          cudaSuccess)
+    return e;
   DecodeArgs a;
   a.m = m;
   a.units = b.units;
@@ -284,6 +296,8 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   a.bar = b.bar;
   a.status = b.status;
   a.prof = b.prof;
+  a.times = b.times;
+  a.n_times = b.n_times;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
   const void* fn = decode_fn(m.d.prec);
   const int nt = decode_threads_of(m.d.prec);

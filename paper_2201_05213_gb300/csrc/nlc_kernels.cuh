@@ -57,7 +57,9 @@ struct CodecBufs {
   StreamRec* st;
   unsigned* bar;                 // 2 words: arrivals, generation
   int* status;
-  unsigned long long* prof = nullptr;  // decoder phase cycle counters (8), optional
+  unsigned long long* prof = nullptr;  // decoder phase cycle counters (16), optional
+  unsigned long long* times = nullptr;  // decoder step end times, optional
+  long long n_times = 0;
 };
 
 // Launchers (return cudaError_t of the launch).

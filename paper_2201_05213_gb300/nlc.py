@@ -39,6 +39,7 @@ EXPORTS = [
     "nlc_rans_encode", "nlc_rans_decode", "nlc_train_step", "nlc_loss_grad",
     "nlc_compress_noalloc", "nlc_decode_profile",
     "nlc_plan_decode", "nlc_plan_run", "nlc_plan_tune", "nlc_plan_destroy",
+    "nlc_decode_step_times",
 ]
 
 
@@ -96,6 +97,7 @@ def load():
             L.nlc_plan_run.argtypes = [p, p, p, p]
             L.nlc_plan_tune.argtypes = [p, p, p, i, p, p, p]
             L.nlc_plan_destroy.argtypes = [p]
+            L.nlc_decode_step_times.argtypes = [p, p, i64]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -186,6 +188,13 @@ def nlc_decode_profile(ctx, enable, read=True):
     out = np.zeros(16, dtype=np.uint64) if read else None
     _check(load().nlc_decode_profile(ctx, int(enable), _ptr(out) if read else None))
     return out
+
+
+def nlc_decode_step_times(ctx, times):
+    """times: int64 CUDA tensor receiving the decoder's step end times (ns), or None."""
+    if times is None:
+        return _check(load().nlc_decode_step_times(ctx, None, 0))
+    return _check(load().nlc_decode_step_times(ctx, _ptr(times), int(times.numel())))
 
 
 def nlc_set_tuning(ctx, px_per_cta, max_ctas=0):

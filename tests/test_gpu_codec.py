@@ -246,3 +246,25 @@ def test_plan_graph_replay_and_tuner():
     for o, i in zip(plan.outs, imgs2):
         assert np.array_equal(o.cpu().numpy(), i)
     plan.close()
+
+
+def test_step_times_give_image_latencies():
+    # the decoder's step end times are non-decreasing, and an image finishes at
+    # its units' last wavefront step (W + (H-1)(h+1) steps, Algorithm 1)
+    h = 2
+    codec, _ = make_codec((h, 32, 1, 10), N.NLC_BF16, seed=2)
+    sizes = [(64, 48), (16, 16), (40, 100)]
+    imgs = images(23, sizes)
+    data, offs = codec.compress([to_dev(i) for i in imgs], 0, 1)
+    steps = [W + (H - 1) * (h + 1) for H, W in sizes]
+    times = torch.full((max(steps) + 5,), -1, dtype=torch.int64, device=DEV)
+    N.nlc_decode_step_times(codec.ctx, times)
+    outs = codec.decompress(data, offs, sizes, 0, 1)
+    N.nlc_decode_step_times(codec.ctx, None)
+    for o, i in zip(outs, imgs):
+        assert np.array_equal(o.cpu().numpy(), i)
+    t = times.cpu().numpy()
+    T = max(steps)
+    assert t[0] > 0 and (np.diff(t[:T + 1]) >= 0).all() and (t[T + 1:] == 0).all()
+    lat = [t[s] - t[0] for s in steps]
+    assert lat[1] <= lat[2] <= lat[0] and lat[0] == t[T] - t[0]
