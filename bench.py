@@ -56,11 +56,12 @@ def workload_name():
 
 
 # DRAM traffic of decode_kernel per decoded pixel from one ncu capture of the
-# small case (1x1024^2: 6.61 MB read + 0.88 MB written for 1,048,576 px), scaled
-# to a launch by its pixels.  It holds only for the kernel sources it was taken
-# on: TRAFFIC_SRC_SHA is their sha256, and any other sources report null.
-TRAFFIC_B_PER_PX = 7.14
-TRAFFIC_SRC_SHA = "0e5c239c1bcd0e10e9f21f397e54fd115bfb3b4658fe2d9fd096107453025aaf"
+# small case at 16 CTAs (1x1024^2: 5.97 MB read + 0.32 MB written for
+# 1,048,576 px), scaled to a launch by its pixels.  It holds only for the
+# kernel sources it was taken on: TRAFFIC_SRC_SHA is their sha256, and any
+# other sources report null.
+TRAFFIC_B_PER_PX = 6.00
+TRAFFIC_SRC_SHA = "9705558ca1305410599fa5472e2cb9b1b86ed8d915c3b2357120a0fea6c47ccd"
 
 
 def _csrc_sha():
@@ -515,7 +516,7 @@ def main():
             "frac": achieved / mufu_peak,
             "traffic": TRAFFIC_B_PER_PX * n_px if _csrc_sha() == TRAFFIC_SRC_SHA else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 1x1024^2 "
-                              "decode, scaled by pixels (bytes per launch)",
+                              "decode at 16 CTAs, scaled by pixels (bytes per launch)",
             "peak_source": f"16 MUFU lanes/clk/SM x 152 SMs x {sm_mhz:.0f} MHz (max SM clock)",
             "work": f"{2 * evals_per_px} MUFU ops/px (search terms only)",
             "tensor": {"achieved_tflops": flops / (ms / 1e3) / 1e12,
