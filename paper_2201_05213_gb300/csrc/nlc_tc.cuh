@@ -2,10 +2,15 @@
 //
 // A tile is M = 128 pixels.  Each layer is one chain of
 // tcgen05.mma.cta_group::1.kind::f16 instructions (K = 16 per instruction,
-// FP32 accumulation in TMEM) issued by one thread; the accumulator is read
-// back with tcgen05.ld by all 8 warps (warp w reads TMEM lanes 32(w%4)..+31
-// and half w/4 of the columns), bias/ELU/residual are applied in registers
-// and the next layer's A operand is written to shared memory as BF16 in the
+// FP32 accumulation in TMEM columns [0, 128)) issued by one thread; the
+// accumulator is read back with tcgen05.ld by all warps (warp w reads TMEM
+// lanes 32(w%4)..+31, i.e. its rows, and 8-column chunks w/4, w/4 + NP, ...),
+// bias/ELU/residual are applied in registers, and the next layer's A
+// operand stays in tensor memory: each thread writes its row's BF16 pairs
+// with tcgen05.st into columns [128, 128 + C/2) (lane m = row m, column
+// 128 + k/2 = elements k, k+1), which the next tcgen05.mma reads as its A
+// operand (8 columns per K step).  The first layer's A operand (the context
+// tile) and every B operand (the weights) are in shared memory, in the
 // canonical no-swizzle K-major layout:
 //   element (r, k) of an R x Kd matrix at
 //   ((r/8) * (Kd/8) + k/8) * 64 + (r%8) * 8 + (k%8)   (BF16 elements)
@@ -27,13 +32,14 @@ namespace nlc {
 
 constexpr int kTcM = 128;
 constexpr int kTileMax = 128;
-constexpr int kTmemCols = 128;
+constexpr int kTmemCols = 256;  // accumulator [0, 128), A operand [128, 128 + C/2)
+constexpr int kAcol = 128;       // first TMEM column of the A operand
 constexpr unsigned kMbarSpin = 1u << 22;
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
 struct TcPlan {
-  int w0, w1[kMaxR], w2[kMaxR], wh, bias, hbuf, p, mbar, tslot, end;
+  int w0, w1[kMaxR], w2[kMaxR], wh, bias, p, mbar, tslot, end;
 };
 
 __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
@@ -51,9 +57,6 @@ __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
   o += d.NOp * d.C * 2;
   p.bias = o;
   o += (d.C + 2 * d.R * d.C + d.NOp) * 4;
-  o = align_up(o, 128);
-  p.hbuf = o;
-  o += kTcM * d.C * 2;
   o = align_up(o, 128);
   p.p = o;  // P[m][ldP] FP32, aliased with the BF16 context tile X
   int pbytes = kTcM * d.ldP * 4, xbytes = kTcM * d.Fp * 2;
@@ -76,7 +79,6 @@ __host__ __device__ inline size_t bias_floats(const Dims& d) { return (size_t)d.
 struct TcSmem {
   unsigned char* base;
   uint16_t* X;
-  uint16_t* H;
   float* P;
   float* bias;
   uint64_t* mbar;
@@ -99,7 +101,6 @@ __device__ __forceinline__ TcSmem tc_carve(const Dims& d, unsigned char* smem) {
   TcSmem t;
   t.base = smem;
   t.X = reinterpret_cast<uint16_t*>(smem + p.p);
-  t.H = reinterpret_cast<uint16_t*>(smem + p.hbuf);
   t.P = reinterpret_cast<float*>(smem + p.p);
   t.bias = reinterpret_cast<float*>(smem + p.bias);
   t.mbar = reinterpret_cast<uint64_t*>(smem + p.mbar);
@@ -350,6 +351,29 @@ __device__ __forceinline__ void tc_issue(const TcSmem& t, uint32_t a_off, uint32
   }
 }
 
+// Layers 1..: A from tensor memory (columns kAcol + 8 s for K step s).
+__device__ __forceinline__ void mma_bf16_ta(uint32_t dtm, uint32_t atm, uint64_t bd,
+                                            uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+      "r"(atm), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_issue_ta(const TcSmem& t, uint32_t b_off, int Kd, int N) {
+  if (threadIdx.x == 0) {
+    fence_after_sync();
+    const uint64_t db = umma_desc(smem_u32(t.base + b_off), 128u, (uint32_t)(Kd / 8) * 128u);
+    const uint32_t idesc = idesc_bf16(kTcM, N);
+    const uint32_t tm = t.tmem, ta = t.tmem + (uint32_t)kAcol;
+    mma_bf16_ta(tm, ta, db, idesc, 0u);  // Kd = C <= 64: at most 4 steps
+    if (Kd / 16 > 1) mma_bf16_ta(tm, ta + 8u, db + 16, idesc, 1u);
+    if (Kd / 16 > 2) mma_bf16_ta(tm, ta + 16u, db + 32, idesc, 1u);
+    if (Kd / 16 > 3) mma_bf16_ta(tm, ta + 24u, db + 48, idesc, 1u);
+    mma_commit(t.mbar);
+  }
+}
+
 __device__ __forceinline__ bool tc_wait(TcSmem& t) {
   bool ok = mbar_wait(t.mbar, t.phase);
   t.phase ^= 1u;
@@ -361,14 +385,16 @@ __device__ __forceinline__ float elu_tc(float x) {
   return x > 0.f ? x : __fsub_rn(ex2_approx(__fmul_rn(x, 1.4426950408889634f)), 1.f);
 }
 
-// Writes 8 values (columns k0..k0+7) of row r into the BF16 H tile.
-__device__ __forceinline__ void store_h8(uint16_t* H, int r, int k0, int C, const float (&v)[8]) {
-  uint4 q;
-  q.x = pack_bf16(v[0], v[1]);
-  q.y = pack_bf16(v[2], v[3]);
-  q.z = pack_bf16(v[4], v[5]);
-  q.w = pack_bf16(v[6], v[7]);
-  *reinterpret_cast<uint4*>(H + umma_off(r, k0, C)) = q;
+// Writes 8 BF16 values (A-operand elements k0..k0+7 of this thread's row)
+// to tensor memory at taddr (4 columns), without waiting (tmem_wait_st).
+__device__ __forceinline__ void tmem_st8_bf16(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(pack_bf16(v[0], v[1])), "r"(pack_bf16(v[2], v[3])), "r"(pack_bf16(v[4], v[5])),
+               "r"(pack_bf16(v[6], v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // 8 consecutive FP32 columns of this thread's TMEM lane, without waiting:
@@ -410,6 +436,7 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
   // a warp whose 32 TMEM lanes hold no valid pixel skips its epilogue
   const bool live = 32 * (warp & 3) < n_valid;
   const uint32_t tl = t.tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t ta = tl + (uint32_t)kAcol;  // this warp's lanes of the A operand
   const int C = d.C, nc = C / 8;
   float a[CH][8];
   bool ok = true;
@@ -443,12 +470,12 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
             if (mode == 1) a[i][e] = __fadd_rn(a[i][e], v);
             u[e] = elu_tc(mode == 2 ? v : a[i][e]);
           }
-          store_h8(t.H, row, 8 * c, C, u);
+          tmem_st8_bf16(ta + (uint32_t)(4 * c), u);
         }
       }
+      tmem_wait_st();
     }
     fence_before_sync();
-    fence_async_smem();
     __syncthreads();
   };
 
@@ -464,13 +491,13 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
     const float* b1 = t.bias + C + 2 * r * C;
     // hidden = ELU(H W1^T + b1)
     tick(15);
-    tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w1[r], C, C);
+    tc_issue_ta(t, (uint32_t)pl.w1[r], C, C);
     ok &= tc_wait(t);
     tick(14);
     hidden(b1, 2);
     // a += H W2^T + b2, H = ELU(a)
     tick(15);
-    tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.w2[r], C, C);
+    tc_issue_ta(t, (uint32_t)pl.w2[r], C, C);
     ok &= tc_wait(t);
     tick(14);
     hidden(b1 + C, 1);
@@ -479,7 +506,7 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
   // head: P = H WH^T + bH, in batches of HB chunks
   const float* bh = t.bias + C + 2 * d.R * C;
   tick(15);
-  tc_issue(t, (uint32_t)pl.hbuf, (uint32_t)pl.wh, C, d.NOp);
+  tc_issue_ta(t, (uint32_t)pl.wh, C, d.NOp);
   ok &= tc_wait(t);
   tick(14);
   if (live) {
