@@ -118,6 +118,26 @@ __device__ __forceinline__ ulonglong2 ld_cg_v2_u64(const unsigned long long* p) 
   asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
   return v;
 }
+// Asynchronous global -> shared copies (cp.async): no register receives the
+// data, so nothing waits for it before cp_async_wait_all.  16 bytes through
+// L2 only (both addresses 16-byte aligned), or 4 bytes (4-byte aligned)
+// that read nothing and write zeros when !ok.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gsrc),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+// Waits for the calling thread's copies; other threads see them after a
+// barrier that includes it.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -136,12 +156,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 constexpr unsigned kSpinLimit = 1u << 25;
 constexpr unsigned kBarPoison = 0x80000000u;
 
-// Thread 0, after the CTA's writes (a __syncthreads() must precede): a
-// release reduction, cumulative over the CTA's writes that the barrier made
-// visible to thread 0, with no wait for a reply.
+// One thread of the CTA, after the CTA's writes (a __syncthreads() must
+// precede): a release reduction, cumulative over the CTA's writes that the
+// barrier made visible to that thread, with no wait for a reply.  The
+// release holds the issuing warp until those writes are visible at GPU
+// scope, so the caller issues it from a warp with nothing else to do.
 __device__ __forceinline__ void grid_arrive(unsigned* count) {
-  if (threadIdx.x == 0)
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
 }
 
 // Thread 0 waits until nblocks * target CTAs have arrived; then the whole CTA

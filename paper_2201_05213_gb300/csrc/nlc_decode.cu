@@ -39,12 +39,13 @@ __device__ __forceinline__ int group_slot(int warp, int l) {
   return gpw * warp + (l % gpw) + NW * gpw * (l / gpw);
 }
 
-// Codes the tile's pixels: per pixel, the R, G|r, B|r,g symbols.  pd holds
-// (in lane l) the prefetched stream state of the warp's l-th pixel.  With pc
-// non-null, thread 0 accumulates its sub-stage cycles in pc[8..12].
+// Codes the tile's pixels: per pixel, the R, G|r, B|r,g symbols.  The
+// pixels' stream records are in t.rec (visible to the warp), their windows
+// are being copied to t.win by the warp's lanes.  With pc non-null, thread 0
+// accumulates its sub-stage cycles in pc[8..12].
 template <int GW, int NW>
 __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, int n,
-                                       const GroupRansDec& pd, long long* pc) {
+                                       long long* pc) {
   constexpr int gpw = 32 / GW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / GW, gl = lane % GW;
@@ -62,15 +63,17 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
     const int s = gpw * warp + grp + NW * gpw * j;
     const bool valid = s < n;
     const int se = valid ? s : s - 1;  // an idle group shadows its neighbour
-    const int src = gpw * j + grp;
     GroupRansDec dec;
-    dec.x = __shfl_sync(0xffffffffu, pd.x, src);
-    dec.pos = __shfl_sync(0xffffffffu, pd.pos, src);
-    dec.end = __shfl_sync(0xffffffffu, pd.end, src);
-    dec.lo = __shfl_sync(0xffffffffu, pd.lo, src);
-    dec.hi = __shfl_sync(0xffffffffu, pd.hi, src);
-    dec.w2 = __shfl_sync(0xffffffffu, pd.w2, src);
-    dec.w3 = __shfl_sync(0xffffffffu, pd.w3, src);
+    {
+      const uint4 q = *reinterpret_cast<const uint4*>(t.rec + se);
+      const ulonglong2 pe = *reinterpret_cast<const ulonglong2*>(&t.rec[se].pos);
+      dec.x = q.x;
+      dec.lo = q.y;
+      dec.hi = q.z;
+      dec.pos = pe.x;
+      dec.end = pe.y;
+    }
+    dec.w2 = dec.w3 = 0;
     dec.used = 0;
     dec.bad = false;
     const PixSlot ps = t.slots[se];
@@ -96,7 +99,10 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       __syncwarp();
       tick(11);
     }
+    cp_async_wait_all();  // the window copies of the warp's lanes
+    __syncwarp();
     if (gl == 0 && valid) {
+      dec.set_window(t.win + 4 * s);
       const Unit U = a.units[ps.unit];
       uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
       px[0] = (uint8_t)v[0];
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   constexpr int NT = decode_threads<PREC>(), NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
   const Dims& d = a.m.d;
-  TileSmem t = carve(d, smem, a.n_units, NT / kGW);
+  TileSmem t = carve(d, smem, a.n_units, NT / kGW, true);
   if constexpr (PREC == PREC_BF16) tc_setup(t.tc);
   load_weights<PREC>(a.m, t);
   if (threadIdx.x == 0) t.flag[0] = 0;
@@ -148,8 +154,9 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
     }
   };
   // slots of the tile of n pixels starting at front position base of step
-  auto fill_slots = [&](int step, long long base, int n) {
-    for (int s = threadIdx.x; s < MT; s += blockDim.x) {
+  // (by the first nt threads)
+  auto fill_slots = [&](int step, long long base, int n, int nt) {
+    for (int s = threadIdx.x; s < MT; s += nt) {
       PixSlot ps{-1, 0, 0, 0};
       if (s < n) {
         const int q = (int)(base + s);
@@ -170,68 +177,78 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   };
   // The schedule of step t + 1 (front sizes, this CTA's share, its first
   // tile's slots) needs no decoded data, so it is computed between arriving
-  // at the grid barrier after step t and waiting for the others.
+  // at the grid barrier after step t and waiting for the others: the last
+  // warp arrives (its release waits for the CTA's writes of step t to
+  // reach GPU scope) while the other warps compute the schedule.
+  const int NS = (int)blockDim.x - 32;
   if (pr) ck = clock64();
-  int F = front_scan(a.units, a.n_units, 0, h, a.sched, t.pre, t.sh);
+  int F = front_scan(a.units, a.n_units, 0, h, a.sched, t.pre, t.sh, (int)blockDim.x);
   tick(0);
   long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
-  if (lo < hi) fill_slots(0, lo, (int)min((long long)MT, hi - lo));
+  if (lo < hi) fill_slots(0, lo, (int)min((long long)MT, hi - lo), (int)blockDim.x);
   __syncthreads();
   tick(1);
   for (int step = 0; step < a.T; step++) {
     for (long long base = lo; base < hi; base += MT) {
       const int n = (int)min((long long)MT, hi - base);
       if (base != lo) {  // further tiles of a large share
-        fill_slots(step, base, n);
+        fill_slots(step, base, n, (int)blockDim.x);
         __syncthreads();
       }
       // A CTA with at most one pixel per warp codes with whole warps (lower
       // latency per pixel); otherwise two pixels per warp.  Both give the
-      // same tables (see cdf_fix).  Lane l of warp w fetches the rANS state
-      // and next 8 bytes of the warp's l-th pixel ahead of the network.
+      // same tables (see cdf_fix).  Lane l of warp w copies the stream record
+      // of the warp's l-th pixel into shared memory ahead of the network,
+      // asynchronously (no register waits for it, so its round trip overlaps
+      // the gather's); after the network, the 12 stream bytes from the
+      // record's pos + 8, read only when the pixel is done.
       const bool wide = n <= NW;
-      GroupRansDec pd;
-      pd.x = 0;
-      pd.pos = pd.end = 0;
-      pd.lo = pd.hi = pd.w2 = pd.w3 = 0;
-      {
-        const int sl = wide ? group_slot<32, NW>(warp, lane) : group_slot<kGW, NW>(warp, lane);
-        if (sl < n) {
-          // the stream's record in one round trip; the window after its 8
-          // bytes is needed only when the pixel is done
-          const StreamRec* r = a.st + t.slots[sl].aux;
-          const uint4 q = ld_cg_v4(reinterpret_cast<const uint4*>(r));
-          const ulonglong2 pe = ld_cg_v2_u64(&r->pos);
-          pd.x = q.x;
-          pd.lo = q.y;
-          pd.hi = q.z;
-          pd.pos = pe.x;
-          pd.end = pe.y;
-          pd.load_window(a.in);
-        }
+      const int sl = wide ? group_slot<32, NW>(warp, lane) : group_slot<kGW, NW>(warp, lane);
+      if (sl < n) {
+        const StreamRec* r = a.st + t.slots[sl].aux;
+        cp_async16(t.rec + sl, r);
+        cp_async16(&t.rec[sl].pos, &r->pos);
       }
       if (pr) pc[5] += 1;
       tick(1);
       tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+      cp_async_wait_all();
+      if (sl < n) {
+        const unsigned long long w0 = (t.rec[sl].pos + 8ull) & ~3ull, end = t.rec[sl].end;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+          const unsigned long long wa = w0 + 4ull * q;
+          cp_async4(t.win + 4 * sl + q, a.in + (wa < end ? wa : 0ull), wa < end);
+        }
+      }
+      __syncwarp();  // the warp's records are visible to all its lanes
       tick(2);
-      if (wide) code_tile<32, NW>(a, t, n, pd, pc);
-      else code_tile<kGW, NW>(a, t, n, pd, pc);
+      if (wide) code_tile<32, NW>(a, t, n, pc);
+      else code_tile<kGW, NW>(a, t, n, pc);
       __syncthreads();
       tick(3);
     }
     if (step + 1 == a.T) break;
     const unsigned target = (unsigned)step + 1u;
-    if (G > 1) grid_arrive(a.bar);
-    F = front_scan(a.units, a.n_units, step + 1, h, a.sched, t.pre, t.sh);
-    tick(0);
-    lo = (long long)F * blockIdx.x / G;
-    hi = (long long)F * (blockIdx.x + 1) / G;
-    if (lo < hi) fill_slots(step + 1, lo, (int)min((long long)MT, hi - lo));
-    tick(1);
+    if ((int)threadIdx.x >= NS) {
+      if (G > 1 && (int)threadIdx.x == NS) grid_arrive(a.bar);
+    } else {
+      F = front_scan(a.units, a.n_units, step + 1, h, a.sched, t.pre, t.sh, NS);
+      tick(0);
+      lo = (long long)F * blockIdx.x / G;
+      hi = (long long)F * (blockIdx.x + 1) / G;
+      if (lo < hi) fill_slots(step + 1, lo, (int)min((long long)MT, hi - lo), NS);
+      tick(1);
+    }
     if (G > 1) {
       if (!grid_wait(a.bar, G, target, a.status, t.flag)) break;
     } else {
       __syncthreads();
+    }
+    if ((int)threadIdx.x >= NS) {
+      F = t.pre[a.n_units];
+      lo = (long long)F * blockIdx.x / G;
+      hi = (long long)F * (blockIdx.x + 1) / G;
     }
     tick(4);
     if (stamp && blockIdx.x == 0 && step + 1 < a.n_times) a.times[step + 1] = global_ns();
@@ -251,7 +268,7 @@ static int decode_threads_of(int prec) {
 }
 
 size_t decode_smem_bytes(const Dims& d, int n_units) {
-  return tile_smem_bytes(d, n_units, decode_threads_of(d.prec) / kGW);
+  return tile_smem_bytes(d, n_units, decode_threads_of(d.prec) / kGW, true);
 }
 
 static const void* decode_fn(int prec) {

@@ -35,10 +35,19 @@ __device__ __forceinline__ int find_unit_stream(const Unit* units, int n, int s)
   return lo;
 }
 
-// Block-wide exclusive scan of one int per thread; returns the exclusive
-// prefix, writes the total to *total (all threads).
-__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Barrier of the first nt threads of the CTA (nt a multiple of 32): the whole
+// CTA's __syncthreads when nt is its size, else named barrier 1.
+__device__ __forceinline__ void part_sync(int nt) {
+  if (nt == (int)blockDim.x) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+}
+
+// Exclusive scan of one int per thread over the first nt threads of the CTA
+// (nt a multiple of 32, only they call it); returns the exclusive prefix,
+// writes the total to *total.
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long* total,
+                                                     int nt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nt >> 5;
   long long x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -46,7 +55,7 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* sh,
     if (lane >= o) x += t;
   }
   if (lane == 31) sh[warp] = x;
-  __syncthreads();
+  part_sync(nt);
   if (warp == 0) {
     long long y = lane < nw ? sh[lane] : 0;
 #pragma unroll
@@ -56,19 +65,22 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* sh,
     }
     if (lane < nw) sh[lane] = y;
   }
-  __syncthreads();
+  part_sync(nt);
   long long excl = x - v + (warp > 0 ? sh[warp - 1] : 0);
   *total = sh[nw - 1];
-  __syncthreads();
+  part_sync(nt);
   return excl;
+}
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long* total) {
+  return block_excl_scan(v, sh, total, (int)blockDim.x);
 }
 
 // Fronts of all units at global step t: pre[u] = exclusive prefix of the
 // front sizes, pre[n_units] = total.  Requires n_units + 1 ints of smem.
+// Computed by (and returned to) the first nt threads of the CTA.
 __device__ __forceinline__ int front_scan(const Unit* __restrict__ units, int n_units, int t,
-                                          int h, int sched,
-                          int* pre, long long* sh) {
-  const int per = (n_units + blockDim.x - 1) / blockDim.x;
+                                          int h, int sched, int* pre, long long* sh, int nt) {
+  const int per = (n_units + nt - 1) / nt;
   const int u0 = threadIdx.x * per, u1 = min(u0 + per, n_units);
   long long sum = 0;
   for (int u = u0; u < u1; u++) {
@@ -77,14 +89,14 @@ __device__ __forceinline__ int front_scan(const Unit* __restrict__ units, int n_
     sum += c;
   }
   long long total;
-  long long run = block_excl_scan(sum, sh, &total);
+  long long run = block_excl_scan(sum, sh, &total, nt);
   for (int u = u0; u < u1; u++) {
     int c = pre[u];
     pre[u] = (int)run;
     run += c;
   }
   if (threadIdx.x == 0) pre[n_units] = (int)total;
-  __syncthreads();
+  part_sync(nt);
   return (int)total;
 }
 
@@ -108,18 +120,10 @@ struct GroupRansDec {
   int used;
   bool bad;
 
-  // w2, w3 from the stream at base: aligned words that hold a byte before
-  // `end` only (so no word outside the stream's container is read).
-  __device__ __forceinline__ void load_window(const uint8_t* base) {
-    const unsigned long long a = pos + 8;
-    const unsigned long long w0 = a & ~3ull;
-    uint32_t v[3];
-#pragma unroll
-    for (int q = 0; q < 3; q++) {
-      const unsigned long long wa = w0 + 4ull * q;
-      v[q] = wa < end ? *reinterpret_cast<const uint32_t*>(base + wa) : 0u;
-    }
-    const uint32_t sh = 8u * (uint32_t)(a & 3ull);
+  // w2, w3 from the three aligned words at (pos + 8) & ~3 (a word is read
+  // only if it starts before `end`, so none outside the stream's container).
+  __device__ __forceinline__ void set_window(const uint32_t* v) {
+    const uint32_t sh = 8u * (uint32_t)((pos + 8ull) & 3ull);
     w2 = __funnelshift_r(v[0], v[1], sh);
     w3 = __funnelshift_r(v[1], v[2], sh);
   }
@@ -205,6 +209,8 @@ struct TileSmem {
   WarpScratch* ws;
   PixSlot* slots;
   int* pre;
+  StreamRec* rec;  // decoder: the tile's stream records (kTileMax)
+  uint32_t* win;   // decoder: per pixel, the 12 stream bytes from pos + 8, word-aligned
   long long* sh;
   long long* pc;  // 16 profiling accumulators (thread 0 only)
   int* flag;
@@ -216,8 +222,10 @@ __device__ __forceinline__ const float* tile_params(const TileSmem& t, const Dim
   return t.U0 + (size_t)m * d.ldP;
 }
 
-// Shared memory of the tile pipeline with `groups` coding groups.
-__host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int groups = kGroups) {
+// Shared memory of the tile pipeline with `groups` coding groups (and, for
+// the decoder, the tile's stream records and windows).
+__host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int groups = kGroups,
+                                                  bool dec = false) {
   size_t bytes;
   if (d.prec == PREC_BF16) {
     bytes = tc_smem_bytes(d);
@@ -227,6 +235,7 @@ __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int 
   }
   bytes = (bytes + 15) & ~(size_t)15;
   bytes += sizeof(WarpScratch) * groups;
+  if (dec) bytes += (sizeof(StreamRec) + 4 * sizeof(uint32_t)) * kTileMax;
   bytes += sizeof(PixSlot) * kTileMax;
   bytes += sizeof(long long) * (33 + 16);
   bytes += sizeof(int) * (n_pre + 1 + 4);
@@ -234,7 +243,7 @@ __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int 
 }
 
 __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, int n_pre,
-                                          int groups = kGroups) {
+                                          int groups = kGroups, bool dec = false) {
   TileSmem t;
   size_t off;
   if (d.prec == PREC_BF16) {
@@ -254,6 +263,14 @@ __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, in
   off = (off + 15) & ~(size_t)15;
   t.ws = reinterpret_cast<WarpScratch*>(smem + off);
   off += sizeof(WarpScratch) * groups;
+  t.rec = nullptr;
+  t.win = nullptr;
+  if (dec) {
+    t.rec = reinterpret_cast<StreamRec*>(smem + off);
+    off += sizeof(StreamRec) * kTileMax;
+    t.win = reinterpret_cast<uint32_t*>(smem + off);
+    off += 4 * sizeof(uint32_t) * kTileMax;
+  }
   t.slots = reinterpret_cast<PixSlot*>(smem + off);
   off += sizeof(PixSlot) * kTileMax;
   t.sh = reinterpret_cast<long long*>(smem + off);
