@@ -56,12 +56,12 @@ def workload_name():
 
 
 # DRAM traffic of decode_kernel per decoded pixel from one ncu capture of the
-# small case at 16 CTAs (1x1024^2: 5.95 MB read + 0.35 MB written for
+# small case at 16 CTAs (1x1024^2: 5.96 MB read + 0.35 MB written for
 # 1,048,576 px), scaled to a launch by its pixels.  It holds only for the
 # kernel sources it was taken on: TRAFFIC_SRC_SHA is their sha256, and any
 # other sources report null.
-TRAFFIC_B_PER_PX = 6.01
-TRAFFIC_SRC_SHA = "d7c38ffac1da7946e750f78e67688f9a0a45db5e9b520421068bf48ae79a0be9"
+TRAFFIC_B_PER_PX = 6.02
+TRAFFIC_SRC_SHA = "b4304dcf8554dd3198b9326133be9653242df28a16d1a72a7609e43c5e08feb5"
 
 
 def _csrc_sha():

@@ -95,29 +95,13 @@ __device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) {
   asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
-__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
-  return v;
-}
 // The GPU's global nanosecond timer.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ uint4 ld_cg_v4(const uint4* p) {
-  uint4 v;
-  asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
-}
-__device__ __forceinline__ ulonglong2 ld_cg_v2_u64(const unsigned long long* p) {
-  ulonglong2 v;
-  asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
-  return v;
-}
+
 // Asynchronous global -> shared copies (cp.async): no register receives the
 // data, so nothing waits for it before cp_async_wait_all.  16 bytes through
 // L2 only (both addresses 16-byte aligned), or 4 bytes (4-byte aligned)

@@ -33,7 +33,7 @@ struct DeviceModel {
 // next 8 stream bytes (b0 = bytes pos .. pos+3, little-endian; b1 = pos+4 ..
 // pos+7; bytes at or past `end` are unspecified and never consumed by a
 // valid stream), the read position and the end (absolute offsets into the
-// batch of containers).  Loaded with two 16-byte loads.
+// batch of containers).  Copied to shared memory with two 16-byte cp.async.
 struct alignas(16) StreamRec {
   uint32_t x, b0, b1, pad;
   unsigned long long pos, end;
