@@ -12,7 +12,8 @@ same GPU (one pixel per image per step, the paper's sequential decoder), the
 encoder's throughput, code lengths (actual bytes and model-ideal), the FP64
 oracle's code length on sampled pixels, a roofline line for the decode
 kernel, an end-to-end number through the C ABI with host buffers, and the
-oracle decoder timed on a bounded sample on the host cores.
+oracle decoder timed on bounded samples on one host core and on all of them
+(one process per core over independent patches).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -255,9 +256,82 @@ def cpu_baseline(w, img, budget_s=12.0):
         dt = time.perf_counter() - t0
         assert ok and (dec == sub).all()
     px = rows * PATCH
-    return {"value": px / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": px / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "rows": rows,
             "sample": f"{rows}x{PATCH} px of the first 256^2 patch of the 2048^2 image, "
                       f"sequential FP64 decode, {dt:.1f} s"}
+
+
+_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+    sys.path.insert(0, ROOT)
+
+
+def _oracle_decode_task(task):
+    """One worker: encode its own unit (untimed), wait for all workers, then
+    time the oracle's sequential decode of it."""
+    import oracle as O
+    w, sub = task
+    words, lens, _, _ = O.encode_image(CFG, w, sub, 0, 1)
+    _BARRIER.wait()
+    t0 = time.perf_counter()
+    dec, ok = O.decode_image(CFG, w, words, lens, sub.shape[0], sub.shape[1], 0, 1)
+    dt = time.perf_counter() - t0
+    return sub.shape[0] * sub.shape[1], dt, bool(ok and (dec == sub).all())
+
+
+def cpu_model():
+    """The host CPU's model (lscpu's "Model name", else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class ParallelOracle:
+    """The oracle's sequential decoder over independent units, one process
+    per online host core (spawned, so safe beside an initialised CUDA
+    context): every worker decodes the first `rows` rows of its own 256x256
+    patch of the 2048^2 image, all starting together; px/s = all workers'
+    pixels / the longest worker's decode time."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.n = os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.n, initializer=_pool_init, initargs=(ctx.Barrier(self.n),))
+
+    def run(self, w, img, rows):
+        per = img.shape[1] // PATCH
+        tasks = []
+        for k in range(self.n):
+            y, x = PATCH * ((k // per) % (img.shape[0] // PATCH)), PATCH * (k % per)
+            tasks.append((w, np.ascontiguousarray(img[y:y + rows, x:x + PATCH])))
+        res = self.pool.map(_oracle_decode_task, tasks, chunksize=1)
+        assert all(r[2] for r in res), "parallel oracle round trip differs"
+        px, dt = sum(r[0] for r in res), max(r[1] for r in res)
+        return {"value": px / dt, "unit": UNIT, "cores": self.n, "kind": "oracle",
+                "cpu": cpu_model(),
+                "sample": f"{self.n} processes, each {rows}x{PATCH} px of its own 256^2 patch "
+                          f"of the 2048^2 image, sequential FP64 decode, {dt:.1f} s"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def run_reference(args):
@@ -267,9 +341,15 @@ def run_reference(args):
     from paper_2201_05213_gb300 import synth
     w = synth.xavier_weights(*CFG, seed=0)
     img = synth.make_image(SEED, 2048, 2048, N_POLY, index=0)
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(w, img, budget_s=4.0))
+    # one core sizes the sample (about 4 s); then every step decodes half as
+    # many rows in each of one process per host core
+    single = cpu_baseline(w, img, budget_s=4.0)
+    rows = max(8, single.pop("rows") // 2)
+    par = ParallelOracle()
+    try:
+        vals = [par.run(w, img, rows) for _ in range(args.warmup + args.steps)]
+    finally:
+        par.close()
     timed = vals[args.warmup:]
     v = float(np.mean([t["value"] for t in timed]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -277,8 +357,10 @@ def run_reference(args):
             "ms_per_step": 1000.0 * (2048 * 2048 + 8 * 1024 * 1024) / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(), "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": timed[-1]["cores"],
+                             "kind": "oracle", "cpu": timed[-1]["cpu"],
                              "sample": timed[-1]["sample"]},
+            "cpu_baseline_one_core": single,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -547,7 +629,14 @@ def main():
             **extra,
         }
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(w.astype(np.float64), imgs[0])
+            w64 = w.astype(np.float64)
+            line["cpu_baseline"] = cpu_baseline(w64, imgs[0])
+            rows = max(8, line["cpu_baseline"].pop("rows") // 2)
+            par = ParallelOracle()
+            try:
+                line["cpu_baseline_all_cores"] = par.run(w64, imgs[0], rows)
+            finally:
+                par.close()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
