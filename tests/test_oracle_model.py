@@ -318,3 +318,88 @@ def test_tiny_workload_oracle_round_trip():
     dec, ok = O.decode_image(cfg, w, words, lens, 32, 32, 0, 0)
     assert ok and (dec == img).all()
     assert 8 * len(words) <= bq + 32 + 1
+
+
+def _mp_scaled(v):
+    return mpmath.mpf(2 * v - 255) / 255
+
+
+@pytest.mark.parametrize("raw", [(0.8, -1.3, 0.45), (-2.0, 0.6, -0.9), (3.0, 3.0, -3.0)])
+def test_single_component_coupled_means_closed_form(raw):
+    # K = 1, nonzero coupling: the G location is mu_G + tanh(a) x_R and the B
+    # location mu_B + tanh(b) x_R + tanh(c) x_G, x = (2v - 255)/255; each
+    # channel's coding distribution is then the plain logistic bin mass there.
+    K = 1
+    p = np.zeros(10)
+    p[1:4] = [0.15, -0.35, 0.6]
+    p[4:7] = [-3.2, -2.7, -3.9]
+    p[7:10] = raw
+    a, b, c = (mpmath.tanh(mpmath.mpf(x)) for x in raw)
+    for r, g in [(17, 230), (255, 0), (128, 64), (0, 255)]:
+        xr, xg = _mp_scaled(r), _mp_scaled(g)
+        loc = [mpmath.mpf(p[1]), p[2] + a * xr, p[3] + b * xr + c * xg]
+        for ch in range(3):
+            for v in (0, 5, 60, 127, 128, 190, 255):
+                got = O.channel_prob(K, p, ch, r, g, v)
+                ref = float(_mp_logistic_mass(loc[ch], p[4 + ch], v))
+                assert abs(got - ref) <= 1e-13 + 1e-10 * ref, (r, g, ch, v, got, ref)
+
+
+def _mp_joint(p, K, r, g, b):
+    """p(r, g, b) of the joint mixture written out in 50-digit arithmetic:
+    sum_k softmax(logits)_k * L(r; mu_R) * L(g; mu_G + tanh(a_k) x_r)
+    * L(b; mu_B + tanh(b_k) x_r + tanh(c_k) x_g), L the logistic bin mass with
+    log-scale max(ls, -7)."""
+    logits = [mpmath.mpf(p[k]) for k in range(K)]
+    z = sum(mpmath.e ** l for l in logits)
+    xr, xg = _mp_scaled(r), _mp_scaled(g)
+    tot = mpmath.mpf(0)
+    for k in range(K):
+        mu = [mpmath.mpf(p[K + c * K + k]) for c in range(3)]
+        ls = [max(float(p[4 * K + c * K + k]), -7.0) for c in range(3)]
+        t = [mpmath.tanh(mpmath.mpf(p[7 * K + c * K + k])) for c in range(3)]
+        pr = _mp_logistic_mass(mu[0], ls[0], r)
+        pg = _mp_logistic_mass(mu[1] + t[0] * xr, ls[1], g)
+        pb = _mp_logistic_mass(mu[2] + t[1] * xr + t[2] * xg, ls[2], b)
+        tot += mpmath.e ** logits[k] / z * pr * pg * pb
+    return tot
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_three_component_coupled_mixture_against_50_digit_joint(seed):
+    K = 3
+    rng = np.random.default_rng(200 + seed)
+    p = _rand_params(K, rng)
+    p[4 * K:7 * K] = rng.uniform(-4, -1, 3 * K)
+    p[7 * K:] = rng.uniform(-2, 2, 3 * K)  # strong coupling of every component
+    p[4 * K] = -7.5  # one log-scale below the clamp
+    for r, g, b in [(40, 200, 90), (255, 0, 128), (0, 0, 0), tuple(int(v) for v in rng.integers(0, 256, 3))]:
+        ref = _mp_joint(p, K, r, g, b)
+        if ref < mpmath.mpf(10) ** -250:
+            continue
+        ref_bits = float(-mpmath.log(ref, 2))
+        assert abs(O.pixel_bits(K, p, r, g, b) - ref_bits) <= 1e-9 * max(1.0, ref_bits)
+        # chain rule: the channel coding distributions multiply to the joint
+        pr = _mp_joint_marg(p, K, r)
+        pg = _mp_joint_marg(p, K, r, g) / pr
+        assert abs(O.channel_prob(K, p, 0, r, g, r) - float(pr)) <= 1e-12 + 1e-9 * float(pr)
+        assert abs(O.channel_prob(K, p, 1, r, g, g) - float(pg)) <= 1e-12 + 1e-9 * float(pg)
+        pb = ref / (pr * pg)
+        assert abs(O.channel_prob(K, p, 2, r, g, b) - float(pb)) <= 1e-12 + 1e-9 * float(pb)
+
+
+def _mp_joint_marg(p, K, r, g=None):
+    """Marginal p(r), or p(r, g), of the joint mixture (the later channels'
+    bin masses sum to one), in 50-digit arithmetic."""
+    logits = [mpmath.mpf(p[k]) for k in range(K)]
+    z = sum(mpmath.e ** l for l in logits)
+    xr = _mp_scaled(r)
+    tot = mpmath.mpf(0)
+    for k in range(K):
+        term = mpmath.e ** logits[k] / z
+        term *= _mp_logistic_mass(mpmath.mpf(p[K + k]), max(float(p[4 * K + k]), -7.0), r)
+        if g is not None:
+            m_g = mpmath.mpf(p[2 * K + k]) + mpmath.tanh(mpmath.mpf(p[7 * K + k])) * xr
+            term *= _mp_logistic_mass(m_g, max(float(p[5 * K + k]), -7.0), g)
+        tot += term
+    return tot
