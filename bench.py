@@ -235,6 +235,185 @@ def heldout_bpd(codec, n=256, seed=5):
     return float(bits.double().sum()) / (3 * 32 * 32 * n)
 
 
+def timed_decode(fn, stream, flush, reps=1):
+    """Mean CUDA-event time (ms) of fn() over reps runs, L2 flushed before each."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
+def mufu_peak(local):
+    """Measured MUFU rate (ops/s) of the search's ex2 + rcp pair at full
+    occupancy, best of three, with the SM clock sampled while it runs."""
+    from paper_2201_05213_gb300 import nlc as N
+    N.nlc_measure_mufu(2000)
+    runs = []
+    with ClockSampler(local) as clk:
+        for _ in range(3):
+            runs.append(N.nlc_measure_mufu(40000))
+    c = clk.summary()
+    rate, ms = max(runs)
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = c["sm_mhz"] or 2070.0
+    return {"ops_per_s": rate, "kernel_ms": ms, "sms": sms, "sm_mhz": c["sm_mhz"],
+            "ops_per_clk_per_sm": rate / (sms * mhz * 1e6), "clocks": c,
+            "how": "nlc_measure_mufu: 8 independent rcp.approx(1 + ex2.approx(x)) chains per "
+                   "thread, 512-thread CTAs at full occupancy on every SM, CUDA events"}
+
+
+def decode_decomposition(codec, imgs, dimgs, data, offs, stream, flush, wave_ms):
+    """The speed-up split into its two sources (Table 2b separates the
+    sequential and wavefront decoders; the patches are this workload's own):
+    raster order inside every patch (one pixel per patch and step), the
+    wavefront on whole images (no patches), and both (the timed decoder)."""
+    import torch
+    from paper_2201_05213_gb300 import nlc as N
+    n_px = sum(i.shape[0] * i.shape[1] for i in imgs)
+    outs = [torch.empty_like(t) for t in dimgs]
+    res = {}
+    # raster inside each patch, same containers
+    plan = codec.plan(SIZES, PATCH, N.NLC_LAYOUT_ROW, N.NLC_SCHED_RASTER, outs=outs)
+    ppc, _ = plan.tune(data, offs, reps=1, stream=stream)
+    ms = timed_decode(lambda: plan.run(data, offs, stream), stream, flush, reps=1)
+    codec.check()
+    for a, b in zip(outs, imgs):
+        assert np.array_equal(a.cpu().numpy(), b), "raster round trip differs"
+    plan.close()
+    res["patch_raster"] = {"value": n_px / (ms / 1e3), "ms": ms, "steps": PATCH * PATCH,
+                           "px_per_cta": ppc, "how": "NLC_SCHED_RASTER on the same patch "
+                           "containers: one pixel per patch per step"}
+    # wavefront on whole images (each image one unit, one stream per row)
+    wdata, woffs = codec.compress(dimgs, 0, N.NLC_LAYOUT_ROW)
+    plan = codec.plan(SIZES, 0, N.NLC_LAYOUT_ROW, N.NLC_SCHED_WAVEFRONT, outs=outs)
+    ppc, _ = plan.tune(wdata, woffs, reps=1, stream=stream)
+    ms = timed_decode(lambda: plan.run(wdata, woffs, stream), stream, flush, reps=2)
+    codec.check()
+    for a, b in zip(outs, imgs):
+        assert np.array_equal(a.cpu().numpy(), b), "whole-image wavefront round trip differs"
+    plan.close()
+    H, W = max(SIZES)
+    res["image_wavefront"] = {"value": n_px / (ms / 1e3), "ms": ms,
+                              "steps": W + (H - 1) * (CFG[0] + 1), "px_per_cta": ppc,
+                              "bytes": int(woffs[-1]),
+                              "how": "NLC_SCHED_WAVEFRONT on whole-image containers"}
+    res["patch_wavefront"] = {"value": n_px / (wave_ms / 1e3), "ms": wave_ms,
+                              "steps": PATCH + (PATCH - 1) * (CFG[0] + 1),
+                              "how": "the timed decoder (both schemes)"}
+    return res
+
+
+def cfg1_wavefront_fp32(w, stream, flush):
+    """64 generator images of 64x64 (seed 1), h=3 C=64 R=2 K=10, FP32 network,
+    the in-run trained weights, one stream per row: wavefront decode against
+    the sequential decode of the same containers on the same GPU."""
+    import torch
+    from paper_2201_05213_gb300 import codec as CD
+    from paper_2201_05213_gb300 import nlc as N
+    from paper_2201_05213_gb300 import synth
+    sizes = [(64, 64)] * 64
+    imgs = synth.make_batch(1, sizes)
+    d = [torch.from_numpy(i).cuda() for i in imgs]
+    codec = CD.Codec(*CFG, N.NLC_FP32, w)
+    data, offs = codec.compress(d, 0, N.NLC_LAYOUT_ROW)
+    n_px = 64 * 64 * 64
+    res = {"workload": "64 x 64^2 RGB (seed 1), whole images, row streams, h=3 C=64 R=2 K=10, "
+                       "FP32 network"}
+    for name, sched in (("wavefront", N.NLC_SCHED_WAVEFRONT), ("sequential", N.NLC_SCHED_SEQUENTIAL)):
+        plan = codec.plan(sizes, 0, N.NLC_LAYOUT_ROW, sched)
+        ppc, _ = plan.tune(data, offs, reps=1, stream=stream)
+        ms = timed_decode(lambda: plan.run(data, offs, stream), stream, flush, reps=3)
+        codec.check()
+        for a, b in zip(plan.outs, imgs):
+            assert np.array_equal(a.cpu().numpy(), b), f"cfg1 {name} round trip differs"
+        plan.close()
+        res[name] = {"value": n_px / (ms / 1e3), "unit": UNIT, "ms": ms, "px_per_cta": ppc,
+                     "steps": 316 if name == "wavefront" else 4096}
+    res["speedup"] = res["sequential"]["ms"] / res["wavefront"]["ms"]
+    _, bits = codec.forward(d, 0, params=False, bits=True)
+    res["bpd"] = {"actual": 8.0 * int(offs[-1]) / (3 * n_px),
+                  "gpu_model": float(bits.double().sum()) / (3 * n_px)}
+    codec.close()
+    return res
+
+
+def cfg2_training(steps):
+    """Training throughput at batch 128 of 32x32 crops (seed 2) for h = 1, 2,
+    3 (C=64, R=2, K=10, BF16 context), and the held-out code length on 256
+    generator images after `steps` steps."""
+    import torch
+    from paper_2201_05213_gb300 import codec as CD
+    from paper_2201_05213_gb300 import nlc as N
+    from paper_2201_05213_gb300 import synth
+    out = {}
+    pool = torch.from_numpy(synth.random_crops(2, 8192, size=32, source=256)).cuda()
+    for h in (1, 2, 3):
+        cfg = (h, CFG[1], CFG[2], CFG[3])
+        codec = CD.Codec(*cfg, N.NLC_BF16, synth.xavier_weights(*cfg, seed=0))
+        g = torch.Generator(device="cpu").manual_seed(2)
+        idx = [torch.randint(0, pool.shape[0], (128,), generator=g).cuda() for _ in range(steps)]
+        for i in idx[:3]:
+            codec.train_step(pool[i].contiguous(), 2e-3, want_loss=False)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        last = None
+        for s_ in range(steps):
+            b = pool[idx[s_]].contiguous()
+            last = codec.train_step(b, 2e-3 if s_ < steps * 3 // 4 else 5e-4,
+                                    want_loss=(s_ == steps - 1))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[f"h{h}"] = {"steps": steps, "batch": 128, "steps_per_s": steps / dt,
+                        "px_per_s": steps * 128 * 1024 / dt, "final_loss_bpd": last,
+                        "heldout_bpd": heldout_bpd(codec)}
+        codec.close()
+    out["heldout"] = "256 generator images of 32x32 (seed 5)"
+    out["timed"] = "wall clock of the steps (data indexing on the GPU included), after 3 warm-ups"
+    return out
+
+
+def model_size_sweep(imgs, dimgs, stream, flush, train_steps):
+    """Table 2a's axis on this workload: decode throughput and code length of
+    the local model with 0, 1 and 3 residual blocks (h=3, C=64, K=10, BF16),
+    each trained in-run like the headline model."""
+    from paper_2201_05213_gb300 import codec as CD
+    from paper_2201_05213_gb300 import nlc as N
+    from paper_2201_05213_gb300 import synth
+    import torch
+    n_px = sum(i.shape[0] * i.shape[1] for i in imgs)
+    res = {}
+    for R in (0, 1, 3):
+        cfg = (CFG[0], CFG[1], R, CFG[3])
+        codec = CD.Codec(*cfg, N.NLC_BF16, synth.xavier_weights(*cfg, seed=0))
+        train_model(codec, train_steps)
+        data, offs = codec.compress(dimgs, PATCH, N.NLC_LAYOUT_ROW)
+        plan = codec.plan(SIZES, PATCH, N.NLC_LAYOUT_ROW)
+        ppc, _ = plan.tune(data, offs, reps=1, stream=stream)
+        ms = timed_decode(lambda: plan.run(data, offs, stream), stream, flush, reps=3)
+        codec.check()
+        for a, b in zip(plan.outs, imgs):
+            assert np.array_equal(a.cpu().numpy(), b), f"R={R} round trip differs"
+        plan.close()
+        _, bits = codec.forward(dimgs, PATCH, params=False, bits=True)
+        res[f"R{R}"] = {"value": n_px / (ms / 1e3), "unit": UNIT, "ms": ms, "px_per_cta": ppc,
+                        "weights": N.nlc_num_weights(*cfg),
+                        "bpd": {"actual": 8.0 * int(offs[-1]) / (3 * n_px),
+                                "gpu_model": float(bits.double().sum()) / (3 * n_px)}}
+        codec.close()
+    res["how"] = ("each model trained in-run on seeded 32x32 crops (batch 64, "
+                  f"{train_steps} steps), then the headline decode (tuned plan)")
+    return res
+
+
 def cpu_baseline(w, img, budget_s=12.0):
     """The oracle's sequential decoder on a bounded sample (first rows of the
     first 256x256 patch, decoded as one unit) on one host core."""
@@ -325,6 +504,7 @@ class ParallelOracle:
         assert all(r[2] for r in res), "parallel oracle round trip differs"
         px, dt = sum(r[0] for r in res), max(r[1] for r in res)
         return {"value": px / dt, "unit": UNIT, "cores": self.n, "kind": "oracle",
+                "pixels": px, "seconds": dt,
                 "cpu": cpu_model(),
                 "sample": f"{self.n} processes, each {rows}x{PATCH} px of its own 256^2 patch "
                           f"of the 2048^2 image, sequential FP64 decode, {dt:.1f} s"}
@@ -351,10 +531,13 @@ def run_reference(args):
     finally:
         par.close()
     timed = vals[args.warmup:]
-    v = float(np.mean([t["value"] for t in timed]))
+    # each step decodes the bounded sample; value = its pixels / its time
+    v = float(np.sum([t["pixels"] for t in timed]) / np.sum([t["seconds"] for t in timed]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * (2048 * 2048 + 8 * 1024 * 1024) / v,
+            "ms_per_step": 1000.0 * float(np.mean([t["seconds"] for t in timed])),
+            "pixels_per_step": int(timed[-1]["pixels"]),
+            "full_workload_ms_extrapolated": 1000.0 * sum(h * w_ for h, w_ in SIZES) / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(), "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": timed[-1]["cores"],
@@ -371,7 +554,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nlc", choices=["nlc", "reference"])
-    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--cfg2-steps", type=int, default=1000,
+                    help="training steps per horizon of the batch-128 training report")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the decomposition, FP32, training and model-size reports")
     ap.add_argument("--no-seq", action="store_true", help="skip the sequential baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
@@ -583,6 +770,25 @@ def main():
                           "heldout": "256 generator images of 32x32 (seed 5)"}
         if not args.no_uneven:
             extra["uneven_batch"] = uneven_batch_report(codec, w.astype(np.float64), stream)
+        if not args.no_extra:
+            extra["decode_decomposition"] = decode_decomposition(codec, imgs, dimgs, data, offs,
+                                                                 stream, flush, ms)
+            if not args.no_seq:
+                seq = extra["sequential_baseline"]["ms"]
+                for k, v in extra["decode_decomposition"].items():
+                    v["speedup_vs_sequential"] = seq / v["ms"]
+            extra["cfg1_wavefront_fp32"] = cfg1_wavefront_fp32(w, stream, flush)
+            extra["cfg2_training"] = cfg2_training(args.cfg2_steps)
+            extra["model_size_sweep"] = model_size_sweep(imgs, dimgs, stream, flush,
+                                                         args.train_steps)
+        if not args.no_cpu:
+            import oracle as O
+            t0 = time.perf_counter()
+            ob, npx_o = O.batch_bits_parallel(CFG, w.astype(np.float64), imgs, PATCH)
+            extra["bpd"]["oracle_model_full"] = ob / (3 * npx_o)
+            extra["bpd"]["oracle_model_full_seconds"] = time.perf_counter() - t0
+            extra["bpd"]["gpu_minus_oracle_full"] = gpu_model_bpd - ob / (3 * npx_o)
+            extra["bpd"]["actual_minus_oracle_full"] = actual_bpd - ob / (3 * npx_o)
 
     peaks, src = _measured_peaks()
     # roofline of the decode kernel: MUFU work of the symbol search, two
@@ -590,21 +796,27 @@ def main():
     evals_per_px = 3 * 2 * 15 * CFG[3]
     mufu_ops = 2.0 * evals_per_px * n_px
     clk = clk.summary()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    mufu_peak = 16 * 152 * sm_mhz * 1e6  # 16 MUFU lanes / clk / SM
+    mufu = mufu_peak(local)
     achieved = mufu_ops / (ms / 1e3)
     flops = 54784.0 * n_px
-    roof = {"bound": "alu", "unit": "MUFU op/s", "achieved": achieved, "peak": mufu_peak,
-            "frac": achieved / mufu_peak,
+    hbm_bytes = total_bytes + 3.0 * n_px  # containers read, pixels written
+    roof = {"bound": "alu", "unit": "MUFU op/s", "achieved": achieved, "peak": mufu["ops_per_s"],
+            "frac": achieved / mufu["ops_per_s"],
             "traffic": TRAFFIC_B_PER_PX * n_px if _csrc_sha() == TRAFFIC_SRC_SHA else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 1x1024^2 "
                               "decode at 16 CTAs, scaled by pixels (bytes per launch)",
-            "peak_source": f"16 MUFU lanes/clk/SM x 152 SMs x {sm_mhz:.0f} MHz (max SM clock)",
+            "peak_source": "measured in this run (nlc_measure_mufu, best of 3)",
+            "mufu_probe": mufu,
             "work": f"{2 * evals_per_px} MUFU ops/px (search terms only)",
             "tensor": {"achieved_tflops": flops / (ms / 1e3) / 1e12,
                        "peak_tflops": peaks.get("bf16_tflops_sustained"),
                        "frac": flops / (ms / 1e3) / 1e12 / peaks.get("bf16_tflops_sustained", 1700),
-                       "peak_source": src}}
+                       "peak_source": f"bf16_tflops_sustained, {src}"},
+            "hbm": {"achieved_gbs": hbm_bytes / (ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": hbm_bytes / (ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                    "bytes_per_launch": hbm_bytes,
+                    "work": "algorithmic: containers read once + 3 B per decoded pixel written",
+                    "peak_source": src}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

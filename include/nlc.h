@@ -20,6 +20,13 @@
  *     library owns only the context and a device workspace that it grows on
  *     demand (so the first call with a larger batch allocates).
  *   - Images are uint8 H x W x 3 (RGB), C-contiguous, row stride 3 W bytes.
+ *     Kernels read image buffers (the inputs of the compress calls and of
+ *     nlc_forward, and the outputs of the decode calls, whose decoded pixels
+ *     are the context of later ones) in naturally aligned 4-byte words: the
+ *     up to 3 bytes before an image's first byte and after its last byte
+ *     that share such a word with it are read and their values ignored.
+ *     Such a word never crosses a page, so any buffer of cudaMalloc or of
+ *     a caching allocator qualifies.
  *     Container buffers (d_out of the compress calls, d_in of
  *     nlc_decompress) must be 16-byte aligned (NLC_ERR_ARG otherwise).
  *   - Calls taking a `stream` are asynchronous on that stream (NULL = the
@@ -201,7 +208,9 @@ int nlc_compress(nlc_ctx* ctx, const nlc_image_in* h_imgs, int n, int patch, int
  * library holds until exit; the caller still owns the images, d_out and
  * d_offsets.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress, with the device current); make that first
- * call before any stream capture.  Batches needing more scratch are rejected
+ * call before any stream capture.  Like nlc_compress, every call copies the
+ * batch's unit table to the device (cudaMemcpyAsync on `stream`) from host
+ * memory that the call owns and releases before it returns.  Batches needing more scratch are rejected
  * with NLC_ERR_CAPACITY before anything is launched.  All calls share the one
  * array, which keeps the last call's contents (nothing in it needs to start
  * at zero): calls that overlap on the GPU, from any context or stream, race,
@@ -291,6 +300,16 @@ int nlc_train_step(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, fl
  * network and of the mixture likelihood. */
 int nlc_loss_grad(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, float* d_loss,
                   float* d_grad, nlc_stream stream);
+
+/* Measurement utility (no counterpart in the paper): the device's rate of
+ * the MUFU instruction pair of one logistic term of the symbol search,
+ * rcp.approx(1 + ex2.approx(z)), in MUFU operations per second.  Runs
+ * independent chains of the pair at full occupancy on every SM, `iters`
+ * pairs per chain (about 2e4 gives ~20 ms on a GB300), timed with CUDA
+ * events on `stream`; synchronous.  h_ms (may be NULL) receives the timed
+ * kernel's duration.  This rate is the denominator of the decoder's MUFU
+ * roofline. */
+int nlc_measure_mufu(int iters, nlc_stream stream, double* h_ops_per_s, double* h_ms);
 
 #ifdef __cplusplus
 }

@@ -54,6 +54,7 @@ def lib():
             L.orc_num_units.argtypes = [i, i, i]
             L.orc_forward_image.argtypes = [i, i, i, i, p, p, i, i, i, p]
             L.orc_forward_pixels.argtypes = [i, i, i, i, p, p, i, i, i, i, p, p, p]
+            L.orc_image_bits.argtypes = [i, i, i, i, p, p, i, i, i, p]
             L.orc_rans_encode.restype = l
             L.orc_rans_encode.argtypes = [l, p, p, p, l]
             L.orc_rans_decode.argtypes = [p, l, l, p, p]
@@ -146,6 +147,47 @@ def forward_pixels(cfg, w, img, ys, xs, patch=0):
     lib().orc_forward_pixels(h, C_, R, K, _ptr(w), _ptr(img), H, W, patch, len(ys), _ptr(ys),
                              _ptr(xs), _ptr(out))
     return out
+
+
+def image_bits(cfg, w, img, patch=0):
+    """Model code length -log2 p (bits) of every pixel of img, [H][W] FP64."""
+    h, C_, R, K = cfg
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W, _ = img.shape
+    out = np.zeros((H, W), dtype=np.float64)
+    w = _w64(w)
+    lib().orc_image_bits(h, C_, R, K, _ptr(w), _ptr(img), H, W, patch, _ptr(out))
+    return out
+
+
+def _bits_task(args):
+    cfg, w, img = args
+    return float(image_bits(cfg, w, img).sum())
+
+
+def batch_bits_parallel(cfg, w, imgs, patch, n_proc=None, units=None):
+    """Total model bits of the coding units of a batch, one spawned process per
+    host core (safe beside a CUDA context).  A unit's bits equal those of its
+    sub-image coded as a whole image (the context is zero outside the unit).
+    units: list of (image index, y0, x0, Hu, Wu), default every unit of every
+    image under the P x P partition (P = patch, 0 = whole images)."""
+    import multiprocessing as mp
+
+    if units is None:
+        units = []
+        for k, im in enumerate(imgs):
+            H, W = im.shape[:2]
+            P = patch if patch > 0 else max(H, W)
+            for y in range(0, H, P):
+                for x in range(0, W, P):
+                    units.append((k, y, x, min(P, H - y), min(P, W - x)))
+    tasks = [(cfg, _w64(w), np.ascontiguousarray(imgs[k][y:y + hu, x:x + wu]))
+             for k, y, x, hu, wu in units]
+    n_proc = n_proc or os.cpu_count() or 1
+    build()
+    with mp.get_context("spawn").Pool(min(n_proc, max(1, len(tasks)))) as pool:
+        parts = pool.map(_bits_task, tasks, chunksize=1)
+    return float(sum(parts)), sum(t[2].shape[0] * t[2].shape[1] for t in tasks)
 
 
 def rans_encode(start, freq):

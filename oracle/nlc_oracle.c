@@ -411,6 +411,32 @@ void orc_forward_pixels(int h, int C, int R, int K, const double *w, const uint8
     act_free(&A);
 }
 
+/* Model code length -log2 p(x_ij) of every pixel of an image under a unit
+ * partition (bits[H][W]): the network outputs of orc_forward_image followed
+ * by orc_pixel_bits, one pixel at a time. */
+void orc_image_bits(int h, int C, int R, int K, const double *w, const uint8_t *img, int H, int W,
+                    int patch, double *bits)
+{
+    orc_cfg cfg = {h, C, R, K};
+    orc_w Wt;
+    orc_act A;
+    split_weights(&cfg, w, &Wt);
+    act_alloc(&cfg, &A);
+    int nu = orc_num_units(H, W, patch);
+    for (int u = 0; u < nu; u++) {
+        int y0, x0, Hu, Wu;
+        unit_of(H, W, patch, u, &y0, &x0, &Hu, &Wu);
+        for (int i = 0; i < Hu; i++)
+            for (int j = 0; j < Wu; j++) {
+                const uint8_t *px = img + ((long)(y0 + i) * W + (x0 + j)) * 3;
+                gather_context(h, img, W, y0, x0, Hu, Wu, i, j, A.x);
+                forward_px(&cfg, &Wt, &A);
+                bits[(long)(y0 + i) * W + (x0 + j)] = orc_pixel_bits(K, A.out, px[0], px[1], px[2]);
+            }
+    }
+    act_free(&A);
+}
+
 /* ------------------------------------------------------------------ */
 /* 32-bit rANS (ANS, Section 2) with byte-wise renormalisation: state x  */
 /* in [2^23, 2^31), 16-bit probability scale (M = 2^16), initial encoder */

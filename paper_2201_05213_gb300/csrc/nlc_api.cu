@@ -469,7 +469,7 @@ extern "C" int nlc_compress_bound(const int32_t* H, const int32_t* W, int n, int
 
 extern "C" int nlc_compress(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch, int layout,
                             uint8_t* d_out, size_t cap, uint64_t* d_offsets, nlc_stream stream) {
-  if (!x || (n > 0 && !imgs) || !d_offsets || (layout != 0 && layout != 1))
+  if (!x || n < 0 || (n > 0 && !imgs) || !d_offsets || (layout != 0 && layout != 1))
     return fail(NLC_ERR_ARG, "bad arguments");
   std::vector<int32_t> H(n), W(n);
   std::vector<const void*> data(n);
@@ -502,7 +502,7 @@ extern "C" int nlc_compress(nlc_ctx* x, const nlc_image_in* imgs, int n, int pat
 extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d_offsets,
                               const nlc_image_out* outs, int n, int patch, int layout,
                               int schedule, nlc_stream stream) {
-  if (!x || (n > 0 && (!outs || !d_in || !d_offsets)) || (layout != 0 && layout != 1))
+  if (!x || n < 0 || (n > 0 && (!outs || !d_in || !d_offsets)) || (layout != 0 && layout != 1))
     return fail(NLC_ERR_ARG, "bad arguments");
   if (schedule < 0 || schedule > 2) return fail(NLC_ERR_ARG, "unknown schedule %d", schedule);
   if (reinterpret_cast<uintptr_t>(d_in) % 16) return fail(NLC_ERR_ARG, "d_in must be 16-byte aligned");
@@ -550,7 +550,7 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
 
 extern "C" int nlc_forward(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch, float* d_params,
                            float* d_bits, nlc_stream stream) {
-  if (!x || (n > 0 && !imgs)) return fail(NLC_ERR_ARG, "bad arguments");
+  if (!x || n < 0 || (n > 0 && !imgs)) return fail(NLC_ERR_ARG, "bad arguments");
   std::vector<int32_t> H(n), W(n);
   std::vector<const void*> data(n);
   std::vector<uint8_t*> ptrs(n);
@@ -682,7 +682,7 @@ static int noalloc_scratch(void** out) {
 extern "C" int nlc_compress_noalloc(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch,
                                     int layout, uint8_t* d_out, size_t cap, uint64_t* d_offsets,
                                     nlc_stream stream) {
-  if (!x || (n > 0 && !imgs) || !d_offsets || (layout != 0 && layout != 1))
+  if (!x || n < 0 || (n > 0 && !imgs) || !d_offsets || (layout != 0 && layout != 1))
     return fail(NLC_ERR_ARG, "bad arguments");
   std::vector<int32_t> H(n), W(n);
   std::vector<const void*> data(n);

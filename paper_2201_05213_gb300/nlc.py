@@ -39,7 +39,7 @@ EXPORTS = [
     "nlc_rans_encode", "nlc_rans_decode", "nlc_train_step", "nlc_loss_grad",
     "nlc_compress_noalloc", "nlc_decode_profile",
     "nlc_plan_decode", "nlc_plan_run", "nlc_plan_tune", "nlc_plan_destroy",
-    "nlc_decode_step_times",
+    "nlc_decode_step_times", "nlc_measure_mufu",
 ]
 
 
@@ -98,6 +98,7 @@ def load():
             L.nlc_plan_tune.argtypes = [p, p, p, i, p, p, p]
             L.nlc_plan_destroy.argtypes = [p]
             L.nlc_decode_step_times.argtypes = [p, p, i64]
+            L.nlc_measure_mufu.argtypes = [i, p, p, p]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -296,3 +297,10 @@ def nlc_loss_grad(ctx, batch, loss, grad, stream=None):
     N, H, W, _ = batch.shape
     return _check(load().nlc_loss_grad(ctx, _ptr(batch), N, H, W, _ptr(loss), _ptr(grad),
                                        _stream(stream)))
+
+
+def nlc_measure_mufu(iters=20000, stream=None):
+    """(MUFU ops/s, kernel ms) of the ex2 + rcp pair at full occupancy."""
+    r, ms = C.c_double(0), C.c_double(0)
+    _check(load().nlc_measure_mufu(int(iters), _stream(stream), C.byref(r), C.byref(ms)))
+    return r.value, ms.value

@@ -7,6 +7,8 @@ code lengths must match the oracle's model (|delta bpd| <= 0.01 FP32,
 tables' ideal length; malformed inputs must be reported, not decoded
 silently.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -161,6 +163,14 @@ def test_malformed_input_is_reported():
     # wavefront on one stream per unit is an argument error
     with pytest.raises(N.NLCError):
         codec.decompress(data, offs, sizes, 0, 0, N.NLC_SCHED_WAVEFRONT)
+    # a negative image count is an argument error of every batch entry point
+    L, ctx = N.load(), codec.ctx
+    p = ctypes.c_void_p(dimgs[0].data_ptr())
+    assert L.nlc_compress(ctx, p, -1, 0, 1, p, 16, p, None) == N.NLC_ERR_ARG
+    assert L.nlc_compress_noalloc(ctx, p, -1, 0, 1, p, 16, p, None) == N.NLC_ERR_ARG
+    assert L.nlc_decompress(ctx, p, p, p, -1, 0, 1, 1, None) == N.NLC_ERR_ARG
+    assert L.nlc_forward(ctx, p, -1, 0, p, None, None) == N.NLC_ERR_ARG
+    assert N.nlc_sync_status(codec.ctx) == N.NLC_OK
 
 
 def test_oracle_decodes_same_partition_same_pixels():

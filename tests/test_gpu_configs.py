@@ -58,6 +58,26 @@ def _sampled_parity(codec, cfg, imgs, dimgs, patch, n, seed, tol, bpd_tol):
     assert abs(gpu_bits - ref_bits) / (3 * n) <= bpd_tol, (gpu_bits / (3 * n), ref_bits / (3 * n))
 
 
+def _unit_bpd_parity(codec, cfg, imgs, dimgs, patch, units, bpd_tol):
+    """Model code length of whole coding units (every pixel of each) against
+    the oracle's, which runs one spawned process per host core."""
+    w = codec.get_weights().astype(np.float64)
+    _, bits = codec.forward(dimgs, patch, params=False, bits=True)
+    base = np.cumsum([0] + [i.shape[0] * i.shape[1] for i in imgs])
+    b = bits.double().cpu().numpy()
+    gpu, npx = 0.0, 0
+    for k, y0, x0, hu, wu in units:
+        W = imgs[k].shape[1]
+        rows = base[k] + (y0 + np.arange(hu))[:, None] * W + x0 + np.arange(wu)[None, :]
+        gpu += float(b[rows].sum())
+        npx += hu * wu
+    ref, n_ref = O.batch_bits_parallel(cfg, w, imgs, patch, units=units)
+    assert n_ref == npx
+    d = abs(gpu - ref) / (3 * npx)
+    assert d <= bpd_tol, (gpu / (3 * npx), ref / (3 * npx))
+    return gpu / (3 * npx), ref / (3 * npx)
+
+
 def _round_trip(codec, imgs, dimgs, patch, layout, schedules):
     data, offs = codec.compress(dimgs, patch, layout)
     sizes = [i.shape[:2] for i in imgs]
@@ -128,6 +148,9 @@ def test_cfg3_uneven_batch_bf16():
     d = [to_dev(i) for i in imgs]
     _round_trip(codec, imgs, d, 0, N.NLC_LAYOUT_ROW, [N.NLC_SCHED_WAVEFRONT])
     _sampled_parity(codec, cfg, imgs, d, 0, 256, 3, 2e-2, 0.03)
+    # every pixel of 32 whole images (every 8th of the batch)
+    units = [(k, 0, 0, sizes[k][0], sizes[k][1]) for k in range(0, 256, 8)]
+    _unit_bpd_parity(codec, cfg, imgs, d, 0, units, 0.03)
 
 
 @pytest.mark.parametrize("h", [1, 2, 3])
@@ -140,3 +163,14 @@ def test_cfg4_large_images_patches_bf16(h):
     d = [to_dev(i) for i in imgs]
     _round_trip(codec, imgs, d, 256, N.NLC_LAYOUT_ROW, [N.NLC_SCHED_WAVEFRONT])
     _sampled_parity(codec, cfg, imgs, d, 256, 192, 4, 2e-2, 0.03)
+    # model code length over whole 256^2 patches: every patch of every image
+    # at h = 3 (12.6 M pixels), one patch per image (a different one each) else
+    if h == 3:
+        units = None
+    else:
+        units = [(k, 256 * ((k + h) % (im.shape[0] // 256)), 256 * ((3 * k) % (im.shape[1] // 256)),
+                  256, 256) for k, im in enumerate(imgs)]
+    if units is None:
+        units = [(k, y, x, 256, 256) for k, im in enumerate(imgs)
+                 for y in range(0, im.shape[0], 256) for x in range(0, im.shape[1], 256)]
+    _unit_bpd_parity(codec, cfg, imgs, d, 256, units, 0.03)

@@ -155,3 +155,12 @@ def test_rans_matches_oracle(nstreams):
         N.nlc_rans_decode(codec.ctx, t(bad.ravel(), np.uint8), stride,
                           t([len(r) for r in ref], np.int32), cum, t(off, np.int64), dsym)
         assert N.nlc_sync_status(codec.ctx) == N.NLC_ERR_CORRUPT
+
+
+def test_mufu_probe_rate_is_plausible():
+    # the roofline denominator: MUFU ops/s of the search's ex2 + rcp pair;
+    # between 1 and 64 operations per clock and SM at the device's clocks
+    rate, ms = N.nlc_measure_mufu(4000)
+    props = torch.cuda.get_device_properties(0)
+    per_clk_sm = rate / (props.multi_processor_count * 2.07e9)
+    assert ms > 0 and 1.0 <= per_clk_sm <= 64.0, per_clk_sm

@@ -403,3 +403,19 @@ def _mp_joint_marg(p, K, r, g=None):
             term *= _mp_logistic_mass(m_g, max(float(p[5 * K + k]), -7.0), g)
         tot += term
     return tot
+
+
+def test_image_bits_is_forward_then_pixel_bits():
+    cfg = (2, 8, 1, 3)
+    w = synth.xavier_weights(*cfg, seed=7) * 2
+    img = synth.make_image(8, 13, 11)
+    for patch in (0, 5):
+        outs = O.forward_image(cfg, w, img, patch=patch)
+        ref = np.array([[O.pixel_bits(cfg[3], outs[i, j], *img[i, j]) for j in range(11)]
+                        for i in range(13)])
+        np.testing.assert_array_equal(O.image_bits(cfg, w, img, patch), ref)
+    # the unit-parallel total over spawned processes equals the serial sum
+    tot, n = O.batch_bits_parallel(cfg, w, [img, img[:7]], 5, n_proc=2)
+    assert n == 13 * 11 + 7 * 11
+    ser = O.image_bits(cfg, w, img, 5).sum() + O.image_bits(cfg, w, img[:7], 5).sum()
+    assert abs(tot - ser) <= 1e-9 * ser

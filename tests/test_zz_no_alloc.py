@@ -37,22 +37,37 @@ def _compress(fn, codec, dimgs, patch, layout, cap):
 @pytest.mark.parametrize("prec,patch,layout", [(N.NLC_BF16, 32, N.NLC_LAYOUT_ROW),
                                                (N.NLC_FP32, 0, N.NLC_LAYOUT_UNIT)])
 def test_noalloc_matches_compress_twice(prec, patch, layout):
-    codec, _ = make_codec((3, 32, 2, 10), prec, seed=21, scale=1.5)
     sizes = [(70, 90), (33, 17), (64, 64)]
     cap = N.nlc_compress_bound(sizes, patch, layout)
-    for call in range(2):  # two calls in a row share (and reuse) the fixed scratch
-        imgs = images(30 + call, sizes)
-        dimgs = [to_dev(i) for i in imgs]
-        ref, ref_offs = _compress(N.nlc_compress, codec, dimgs, patch, layout, cap)
-        got, got_offs = _compress(N.nlc_compress_noalloc, codec, dimgs, patch, layout, cap)
-        assert torch.equal(got_offs, ref_offs)
+    batches = [[to_dev(i) for i in images(30 + call, sizes)] for call in range(2)]
+    # A first call on another context loads the library's kernels and its
+    # scratch array on this device, so that what follows measures the calls.
+    warm, _ = make_codec((3, 32, 2, 10), prec, seed=21, scale=1.5)
+    _compress(N.nlc_compress_noalloc, warm, batches[0], patch, layout, cap)
+    warm.close()
+    # A fresh context has an empty workspace: two calls in a row on it must
+    # leave the device's free memory unchanged (no allocation anywhere).
+    codec, _ = make_codec((3, 32, 2, 10), prec, seed=21, scale=1.5)
+    outs = [torch.full((cap,), 0xAB, dtype=torch.uint8, device=DEV) for _ in range(2)]
+    offs = [torch.zeros(len(sizes) + 1, dtype=torch.int64, device=DEV) for _ in range(2)]
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for call in range(2):
+        N.nlc_compress_noalloc(codec.ctx, batches[call], patch, layout, outs[call], offs[call])
+        assert N.nlc_sync_status(codec.ctx) == N.NLC_OK
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"device free memory moved by {free0 - free1} bytes"
+    # then the allocating entry point on the same context, same inputs
+    for call in range(2):
+        ref, ref_offs = _compress(N.nlc_compress, codec, batches[call], patch, layout, cap)
+        assert torch.equal(offs[call], ref_offs)
         end = int(ref_offs[-1])
-        assert torch.equal(got[:end], ref[:end])
-        outs = codec.decompress(got, got_offs, sizes, patch, layout,
-                                N.NLC_SCHED_WAVEFRONT if layout == N.NLC_LAYOUT_ROW
-                                else N.NLC_SCHED_SEQUENTIAL)
-        for a, b in zip(outs, imgs):
-            assert np.array_equal(a.cpu().numpy(), b)
+        assert torch.equal(outs[call][:end], ref[:end])
+        dec = codec.decompress(outs[call], offs[call], sizes, patch, layout,
+                               N.NLC_SCHED_WAVEFRONT if layout == N.NLC_LAYOUT_ROW
+                               else N.NLC_SCHED_SEQUENTIAL)
+        for a, b in zip(dec, batches[call]):
+            assert torch.equal(a, b)
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
