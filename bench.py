@@ -771,16 +771,22 @@ def main():
         if not args.no_uneven:
             extra["uneven_batch"] = uneven_batch_report(codec, w.astype(np.float64), stream)
         if not args.no_extra:
-            extra["decode_decomposition"] = decode_decomposition(codec, imgs, dimgs, data, offs,
-                                                                 stream, flush, ms)
-            if not args.no_seq:
+            def report(key, fn):  # a failing report is recorded, the line still prints
+                try:
+                    extra[key] = fn()
+                except Exception as e:  # noqa: BLE001
+                    extra[key] = {"error": f"{type(e).__name__}: {e}"[:400]}
+                    print(f"bench: report {key} failed: {e}", file=sys.stderr)
+            report("decode_decomposition",
+                   lambda: decode_decomposition(codec, imgs, dimgs, data, offs, stream, flush, ms))
+            if not args.no_seq and "error" not in extra["decode_decomposition"]:
                 seq = extra["sequential_baseline"]["ms"]
                 for k, v in extra["decode_decomposition"].items():
                     v["speedup_vs_sequential"] = seq / v["ms"]
-            extra["cfg1_wavefront_fp32"] = cfg1_wavefront_fp32(w, stream, flush)
-            extra["cfg2_training"] = cfg2_training(args.cfg2_steps)
-            extra["model_size_sweep"] = model_size_sweep(imgs, dimgs, stream, flush,
-                                                         args.train_steps)
+            report("cfg1_wavefront_fp32", lambda: cfg1_wavefront_fp32(w, stream, flush))
+            report("cfg2_training", lambda: cfg2_training(args.cfg2_steps))
+            report("model_size_sweep",
+                   lambda: model_size_sweep(imgs, dimgs, stream, flush, args.train_steps))
         if not args.no_cpu:
             import oracle as O
             t0 = time.perf_counter()

@@ -297,9 +297,27 @@ int nlc_train_step(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, fl
 
 /* Loss (bits per dimension, d_loss: 1 float) and its gradient with respect
  * to the FP32 weights (d_grad: nlc_num_weights floats) -- the adjoint of the
- * network and of the mixture likelihood. */
+ * network and of the mixture likelihood (Eq. 2).  A BF16 context computes
+ * the forward and the adjoint on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation; the mixture likelihood and its gradient in FP32) when
+ * its tiles fit in one CTA's shared memory (every h and K <= 12 with C = 64
+ * and n_res <= 3); FP32 contexts and larger BF16 models use the FP32 SIMT
+ * adjoint.  Deterministic: the same inputs give the same bits. */
 int nlc_loss_grad(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, float* d_loss,
                   float* d_grad, nlc_stream stream);
+
+/* Adjoint of the local network alone (Section 2.1): given the gradient
+ * d_dparams (N H W x 10K floats, the layout of nlc_forward's outputs for the
+ * N images of d_batch, each one unit) of some scalar with respect to the
+ * network outputs, writes its gradient with respect to the FP32 weights to
+ * d_dweights (nlc_num_weights floats).  Same arithmetic and path choice as
+ * nlc_loss_grad (the BF16 path rounds d_dparams to BF16). */
+int nlc_backward(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, const float* d_dparams,
+                 float* d_dweights, nlc_stream stream);
+
+/* Replaces the weights with n_weights FP32 values from device memory
+ * (asynchronous on `stream`; the optimizer state is kept). */
+int nlc_load_weights(nlc_ctx* ctx, const float* d_weights, size_t n_weights, nlc_stream stream);
 
 /* Measurement utility (no counterpart in the paper): the device's rate of
  * the MUFU instruction pair of one logistic term of the symbol search,

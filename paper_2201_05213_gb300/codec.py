@@ -91,6 +91,13 @@ class Codec:
     def train_step(self, batch, lr, want_loss=True, stream=None):
         return N.nlc_train_step(self.ctx, batch, lr, stream, want_loss)
 
+    def backward(self, batch, dparams, stream=None):
+        """Weight gradient of sum(dparams * network outputs) over the batch."""
+        dw = torch.empty(self.n_weights, dtype=torch.float32, device=batch.device)
+        N.nlc_backward(self.ctx, batch, dparams, dw, stream)
+        self.check(stream)
+        return dw
+
     def loss_grad(self, batch, stream=None):
         loss = torch.empty(1, dtype=torch.float32, device=batch.device)
         grad = torch.empty(self.n_weights, dtype=torch.float32, device=batch.device)
@@ -140,21 +147,48 @@ class DecodePlan:
             pass
 
 
-class LocalModelNLL(torch.autograd.Function):
-    """Mean code length (bits per dimension) of a uint8 batch as a function of
-    the FP32 weights; backward is the library's hand-written adjoint."""
+def _batch_images(batch):
+    return [batch[n] for n in range(batch.shape[0])]
+
+
+class LocalModel(torch.autograd.Function):
+    """Network outputs (N H W x 10K, the layout of nlc_forward) of a uint8
+    batch (N x H x W x 3, each image one unit) as a function of the FP32
+    weights (a CUDA tensor); backward maps the outputs' gradient to the
+    weights' with the library's adjoint (nlc_backward)."""
 
     @staticmethod
     def forward(ctx, weights, codec, batch):
-        codec.set_weights(weights.detach().cpu().numpy())
+        N.nlc_load_weights(codec.ctx, weights.detach().contiguous())
+        P, _ = codec.forward(_batch_images(batch), 0)
+        ctx.codec, ctx.batch = codec, batch
+        return P
+
+    @staticmethod
+    def backward(ctx, gP):
+        codec = ctx.codec
+        dw = torch.empty(codec.n_weights, dtype=torch.float32, device=gP.device)
+        N.nlc_backward(codec.ctx, ctx.batch, gP.contiguous().float(), dw)
+        codec.check()
+        return dw, None, None
+
+
+class LocalModelNLL(torch.autograd.Function):
+    """Mean code length (bits per dimension) of a uint8 batch as a function of
+    the FP32 weights (a CUDA tensor); backward is the library's hand-written
+    adjoint of the mixture likelihood and the network."""
+
+    @staticmethod
+    def forward(ctx, weights, codec, batch):
+        N.nlc_load_weights(codec.ctx, weights.detach().contiguous())
         loss, grad = codec.loss_grad(batch)
         ctx.save_for_backward(grad)
-        return loss[0].to(weights.device)
+        return loss[0]
 
     @staticmethod
     def backward(ctx, g):
         (grad,) = ctx.saved_tensors
-        return (g * grad).to(g.device), None, None
+        return g * grad, None, None
 
 
 def ideal_bits_from_tables(cum, pixels):

@@ -612,19 +612,48 @@ extern "C" int nlc_rans_decode(nlc_ctx* x, const uint8_t* d_bytes, int64_t strid
 // ---------------------------------------------------------------------
 // Training
 // ---------------------------------------------------------------------
+// The adjoint of a batch: BF16 contexts on the tensor cores (when the
+// model's tiles fit in a CTA), FP32 contexts (and larger BF16 models) on the
+// FP32 SIMT path.  dparams == nullptr: gradient of the mean code length.
+static int run_adjoint(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W,
+                       const float* d_dparams, float* d_loss, float* d_grad, cudaStream_t s) {
+  const long long npx = (long long)N * H * W;
+  if (npx > (1LL << 31) / 16) return fail(NLC_ERR_UNSUPPORTED, "batch too large");
+  const bool tc = x->d.prec == NLC_BF16 && tc_train_fits(x->d);
+  const size_t need = tc ? tc_train_ws_bytes(x->d, npx, x->sm_count)
+                         : train_ws_bytes(x->d, npx, x->sm_count);
+  int rc = ensure_ws(x, need);
+  if (rc) return rc;
+  if ((rc = ensure_packed(x, s))) return rc;
+  if (tc)
+    CUDA_TRY(launch_tc_train(x->d, x->d_umma, x->d_bias, d_batch, N, H, W, d_dparams, d_loss,
+                             d_grad, x->ws, x->sm_count, x->d_status, s));
+  else
+    CUDA_TRY(launch_loss_grad(x->d, x->d_w, x->d_simt, d_batch, N, H, W, d_dparams, d_loss,
+                              d_grad, x->ws, x->sm_count, s));
+  return NLC_OK;
+}
+
 extern "C" int nlc_loss_grad(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W,
                              float* d_loss, float* d_grad, nlc_stream stream) {
   if (!x || N < 1 || H < 1 || W < 1 || !d_batch || !d_loss || !d_grad)
     return fail(NLC_ERR_ARG, "bad arguments");
+  return run_adjoint(x, d_batch, N, H, W, nullptr, d_loss, d_grad, (cudaStream_t)stream);
+}
+
+extern "C" int nlc_backward(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W,
+                            const float* d_dparams, float* d_dweights, nlc_stream stream) {
+  if (!x || N < 1 || H < 1 || W < 1 || !d_batch || !d_dparams || !d_dweights)
+    return fail(NLC_ERR_ARG, "bad arguments");
+  return run_adjoint(x, d_batch, N, H, W, d_dparams, nullptr, d_dweights, (cudaStream_t)stream);
+}
+
+extern "C" int nlc_load_weights(nlc_ctx* x, const float* d_w, size_t n, nlc_stream stream) {
+  if (!x || !d_w || n != x->n_w) return fail(NLC_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
-  const long long npx = (long long)N * H * W;
-  const size_t need = train_ws_bytes(x->d, npx, x->sm_count);
-  int rc = ensure_ws(x, need);
-  if (rc) return rc;
-  if ((rc = ensure_packed(x, s))) return rc;
-  CUDA_TRY(launch_loss_grad(x->d, x->d_w, x->d_simt, d_batch, N, H, W, d_loss, d_grad, x->ws,
-                            x->sm_count, s));
-  return NLC_OK;
+  CUDA_TRY(cudaMemcpyAsync(x->d_w, d_w, n * 4, cudaMemcpyDeviceToDevice, s));
+  x->dirty = true;
+  return ensure_packed(x, s);
 }
 
 extern "C" int nlc_train_step(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W, float lr,

@@ -162,10 +162,14 @@ __device__ float pixel_nll_grad(const float* P, int K, int r, int g, int b, floa
   return nll;
 }
 
+// dparams == nullptr: dP = gradient of the batch's mean code length (bits
+// per dimension); else dP = dparams [n_px][10K] (an upstream gradient of the
+// network outputs, raster order of the batch) and no loss is computed.
 __global__ void __launch_bounds__(kThreads, 1)
     loss_grad_kernel(Dims d, const float* __restrict__ w, const float* __restrict__ wt,
                      const uint8_t* __restrict__ batch, int N, int H, int W,
-                     float* __restrict__ part_g, float* __restrict__ part_l, int n_w) {
+                     const float* __restrict__ dparams, float* __restrict__ part_g,
+                     float* __restrict__ part_l, int n_w) {
   extern __shared__ __align__(16) float sm[];
   const TrainPlan pl = train_plan(d);
   float* X = sm + pl.X;
@@ -269,6 +273,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int m = warp; m < kTM; m += kWarps) {
       const PixSlot s = slots[m];
       if (s.unit < 0) continue;
+      if (dparams) {
+        const long long q = tile * kTM + m;
+        for (int k = lane; k < NO; k += 32) DP[k * kTM + m] = dparams[q * NO + k];
+        continue;
+      }
       const uint8_t* px = batch + ((long long)s.unit * HW + (long long)s.i * W + s.j) * 3;
       const float nll = pixel_nll_grad(P + (size_t)m * ldP, K, px[0], px[1], px[2], scale, DP, m,
                                        d.NOp, lane);
@@ -332,11 +341,19 @@ __global__ void reduce_grad_kernel(const float* __restrict__ part_g, const float
     for (int b = 0; b < nblk; b++) s = __fadd_rn(s, part_g[(size_t)b * n_w + i]);
     grad[i] = s;
   }
-  if (i == 0) {
+  if (i == 0 && part_l && loss) {
     float s = 0.f;
     for (int b = 0; b < nblk; b++) s = __fadd_rn(s, part_l[b]);
     *loss = s * inv_dims;
   }
+}
+
+cudaError_t launch_reduce_grad(const float* part_g, const float* part_l, int nblk, int n_w,
+                               long long n_px, float* grad, float* loss, cudaStream_t s) {
+  const float inv_dims = 1.f / (0.6931471805599453f * 3.f * (float)n_px);
+  reduce_grad_kernel<<<(n_w + 255) / 256, 256, 0, s>>>(part_g, part_l, nblk, n_w, inv_dims, grad,
+                                                      loss);
+  return cudaGetLastError();
 }
 
 static int train_grid(long long n_px, int sm_count) {
@@ -352,8 +369,8 @@ size_t train_ws_bytes(const Dims& d, long long n_px, int sm_count) {
 }
 
 cudaError_t launch_loss_grad(const Dims& d, const float* w, const float* wt, const uint8_t* batch,
-                             int N, int H, int W, float* loss, float* grad, void* ws, int sm_count,
-                             cudaStream_t s) {
+                             int N, int H, int W, const float* dparams, float* loss, float* grad,
+                             void* ws, int sm_count, cudaStream_t s) {
   const int n_w = (int)((size_t)d.C * d.F + d.C + (size_t)d.R * (2 * d.C * d.C + 2 * d.C) +
                         (size_t)d.NO * d.C + d.NO);
   const long long n_px = (long long)N * H * W;
@@ -365,11 +382,10 @@ cudaError_t launch_loss_grad(const Dims& d, const float* w, const float* wt, con
   if (e != cudaSuccess) return e;
   float* part_g = reinterpret_cast<float*>(ws);
   float* part_l = part_g + (size_t)g * n_w;
-  loss_grad_kernel<<<g, kThreads, smem, s>>>(d, w, wt, batch, N, H, W, part_g, part_l, n_w);
+  loss_grad_kernel<<<g, kThreads, smem, s>>>(d, w, wt, batch, N, H, W, dparams, part_g, part_l,
+                                              n_w);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const float inv_dims = 1.f / (0.6931471805599453f * 3.f * (float)n_px);
-  reduce_grad_kernel<<<(n_w + 255) / 256, 256, 0, s>>>(part_g, part_l, g, n_w, inv_dims, grad, loss);
-  return cudaGetLastError();
+  return launch_reduce_grad(part_g, dparams ? nullptr : part_l, g, n_w, n_px, grad, loss, s);
 }
 
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,

@@ -39,7 +39,7 @@ EXPORTS = [
     "nlc_rans_encode", "nlc_rans_decode", "nlc_train_step", "nlc_loss_grad",
     "nlc_compress_noalloc", "nlc_decode_profile",
     "nlc_plan_decode", "nlc_plan_run", "nlc_plan_tune", "nlc_plan_destroy",
-    "nlc_decode_step_times", "nlc_measure_mufu",
+    "nlc_decode_step_times", "nlc_measure_mufu", "nlc_backward", "nlc_load_weights",
 ]
 
 
@@ -99,6 +99,8 @@ def load():
             L.nlc_plan_destroy.argtypes = [p]
             L.nlc_decode_step_times.argtypes = [p, p, i64]
             L.nlc_measure_mufu.argtypes = [i, p, p, p]
+            L.nlc_backward.argtypes = [p, p, i, i, i, p, p, p]
+            L.nlc_load_weights.argtypes = [p, p, sz, p]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -304,3 +306,16 @@ def nlc_measure_mufu(iters=20000, stream=None):
     r, ms = C.c_double(0), C.c_double(0)
     _check(load().nlc_measure_mufu(int(iters), _stream(stream), C.byref(r), C.byref(ms)))
     return r.value, ms.value
+
+
+def nlc_backward(ctx, batch, dparams, dweights, stream=None):
+    """Weight gradient (dweights, device) of sum(dparams * outputs) over the
+    N x H x W x 3 uint8 batch (dparams: N H W x 10K FP32, device)."""
+    N_, H, W, _ = batch.shape
+    _check(load().nlc_backward(ctx, _ptr(batch), N_, H, W, _ptr(dparams), _ptr(dweights),
+                               _stream(stream)))
+
+
+def nlc_load_weights(ctx, weights, stream=None):
+    """Weights from a device FP32 tensor (asynchronous)."""
+    _check(load().nlc_load_weights(ctx, _ptr(weights), int(weights.numel()), _stream(stream)))

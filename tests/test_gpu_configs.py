@@ -120,22 +120,29 @@ def test_cfg1_wavefront_fp32_trained():
 
 @pytest.mark.parametrize("h", [1, 2, 3])
 def test_cfg2_training_batch(h):
-    # batch 128 of 32x32 crops (seed 2), C=64 K=10: the fused forward's loss on
-    # the whole batch, and the adjoint's gradient on its first 16 crops, match
-    # the oracle (the trainer computes in FP32)
+    # batch 128 of 32x32 crops (seed 2), C=64 K=10, BF16 forward and adjoint
+    # on the tensor cores with FP32 accumulation: the loss of the whole batch
+    # within the BF16 code-length tolerance (0.03 bpd) of the oracle's, the
+    # gradient of the whole batch within the BF16 tolerance of
+    # test_gpu_train.py (relative L2 error <= 3e-2, every element within 5e-2
+    # of the largest); the FP32 context's adjoint on the same batch matches
+    # the oracle to 1e-4 of the largest element
     cfg = (h, 64, 2, 10)
     codec, w = make_codec(cfg, N.NLC_BF16, seed=0)
     w64 = w.astype(np.float64)
     batch = synth.random_crops(2, 128, size=32, source=256)
-    loss, _ = codec.loss_grad(to_dev(batch))
-    ref_loss = O.nll_grad(cfg, w64, batch, False)
-    assert abs(float(loss[0]) - ref_loss) <= 1e-5 * ref_loss
-    sub = np.ascontiguousarray(batch[:16])
-    _, grad = codec.loss_grad(to_dev(sub))
-    _, ref_grad = O.nll_grad(cfg, w64, sub)
+    loss, grad = codec.loss_grad(to_dev(batch))
+    ref_loss, ref_grad = O.nll_grad(cfg, w64, batch)
+    assert abs(float(loss[0]) - ref_loss) <= 0.03, (float(loss[0]), ref_loss)
     g = grad.double().cpu().numpy()
-    scale = np.abs(ref_grad).max()
-    assert np.abs(g - ref_grad).max() <= 1e-4 * scale, np.abs(g - ref_grad).max() / scale
+    rel = np.linalg.norm(g - ref_grad) / np.linalg.norm(ref_grad)
+    worst = np.abs(g - ref_grad).max() / np.abs(ref_grad).max()
+    assert rel <= 3e-2 and worst <= 5e-2, (rel, worst)
+    f32, _ = make_codec(cfg, N.NLC_FP32, seed=0)
+    loss32, grad32 = f32.loss_grad(to_dev(batch))
+    assert abs(float(loss32[0]) - ref_loss) <= 1e-5 * ref_loss
+    g32 = grad32.double().cpu().numpy()
+    assert np.abs(g32 - ref_grad).max() <= 1e-4 * np.abs(ref_grad).max()
 
 
 def test_cfg3_uneven_batch_bf16():
