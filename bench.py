@@ -414,6 +414,30 @@ def model_size_sweep(imgs, dimgs, stream, flush, train_steps):
     return res
 
 
+def sampler_report(codec, stream, flush):
+    """Sampling from the model with the same schedules (Section 5): the
+    headline workload's image sizes and 256^2 patches, wavefront and raster
+    order inside the patches; the samples' own code length under the model."""
+    import torch
+    from paper_2201_05213_gb300 import nlc as N
+    outs = [torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for H, W in SIZES]
+    n_px = sum(H * W for H, W in SIZES)
+    res = {}
+    for name, sched, reps in (("wavefront", N.NLC_SCHED_WAVEFRONT, 3),
+                              ("patch_raster", N.NLC_SCHED_RASTER, 1)):
+        codec.sample(SIZES, PATCH, 7, sched, stream, outs)  # warm-up and set-up
+        ms = timed_decode(lambda: N.nlc_sample(codec.ctx, outs, PATCH, 7, sched, stream), stream,
+                          flush, reps)
+        codec.check()
+        res[name] = {"value": n_px / (ms / 1e3), "unit": "sampled px/s", "ms": ms}
+    _, bits = codec.forward(outs, PATCH, params=False, bits=True)
+    res["sample_bpd"] = float(bits.double().sum()) / (3 * n_px)
+    res["speedup"] = res["patch_raster"]["ms"] / res["wavefront"]["ms"]
+    res["how"] = ("nlc_sample: the decoder's schedule, network and tables, each symbol the "
+                  "inverse CDF of its table at a SplitMix64 counter-based uniform (seed 7)")
+    return res
+
+
 def cpu_baseline(w, img, budget_s=12.0):
     """The oracle's sequential decoder on a bounded sample (first rows of the
     first 256x256 patch, decoded as one unit) on one host core."""
@@ -787,6 +811,7 @@ def main():
             report("cfg2_training", lambda: cfg2_training(args.cfg2_steps))
             report("model_size_sweep",
                    lambda: model_size_sweep(imgs, dimgs, stream, flush, args.train_steps))
+            report("sampler", lambda: sampler_report(codec, stream, flush))
         if not args.no_cpu:
             import oracle as O
             t0 = time.perf_counter()

@@ -260,6 +260,19 @@ int nlc_plan_tune(nlc_plan* plan, const uint8_t* d_in, const uint64_t* d_offsets
 /* Frees the plan (synchronises the device). */
 int nlc_plan_destroy(nlc_plan* plan);
 
+/* Draws n images from the model (Section 5: the parallel schedules serve
+ * sampling from a local autoregressive model as they serve decoding): the
+ * decoder's schedule, network and quantised tables, with each symbol taken
+ * by inverse-CDF sampling of its channel's table, v such that cum_v <= u <
+ * cum_{v+1}, where u is the top 16 bits of output k of SplitMix64 (Steele,
+ * Lea, Flood 2014) seeded with `seed`, k = ((i 2^21 + y) 2^21 + x) 3 + c for
+ * channel c of pixel (y, x) of image i of the batch.  Every schedule gives
+ * the same images.  h_outs as nlc_decompress (caller-allocated, sides and n
+ * below 2^21); `patch` partitions them into independent units as in the
+ * codec (0 = whole images). */
+int nlc_sample(nlc_ctx* ctx, const nlc_image_out* h_outs, int n, int patch, uint64_t seed,
+               int schedule, nlc_stream stream);
+
 /* Network outputs (d_params: sum H W x 10K floats, images in order, pixels
  * in raster order) and/or the model code length -log2 p(x_ij) of every pixel
  * (d_bits: sum H W floats); either may be NULL.  Context zero outside the
@@ -300,9 +313,10 @@ int nlc_train_step(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, fl
  * network and of the mixture likelihood (Eq. 2).  A BF16 context computes
  * the forward and the adjoint on the tensor cores (tcgen05, BF16 operands,
  * FP32 accumulation; the mixture likelihood and its gradient in FP32) when
- * its tiles fit in one CTA's shared memory (every h and K <= 12 with C = 64
- * and n_res <= 3); FP32 contexts and larger BF16 models use the FP32 SIMT
- * adjoint.  Deterministic: the same inputs give the same bits. */
+ * its tiles fit in one CTA's shared memory (every h and K with C <= 64 and
+ * n_res <= 3, and C <= 48 with n_res = 4); FP32 contexts use the FP32 SIMT
+ * adjoint, which holds models up to n_res = 2 at C = 64 (larger ones:
+ * NLC_ERR_UNSUPPORTED).  Deterministic: the same inputs give the same bits. */
 int nlc_loss_grad(nlc_ctx* ctx, const uint8_t* d_batch, int N, int H, int W, float* d_loss,
                   float* d_grad, nlc_stream stream);
 

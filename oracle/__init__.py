@@ -55,6 +55,12 @@ def lib():
             L.orc_forward_image.argtypes = [i, i, i, i, p, p, i, i, i, p]
             L.orc_forward_pixels.argtypes = [i, i, i, i, p, p, i, i, i, i, p, p, p]
             L.orc_image_bits.argtypes = [i, i, i, i, p, p, i, i, i, p]
+            u64 = C.c_uint64
+            L.orc_splitmix64.restype = u64
+            L.orc_splitmix64.argtypes = [u64, u64]
+            L.orc_sample_u16.restype = C.c_uint32
+            L.orc_sample_u16.argtypes = [u64, i, i, i, i]
+            L.orc_sample_image.argtypes = [i, i, i, i, p, i, i, i, u64, i, p]
             L.orc_rans_encode.restype = l
             L.orc_rans_encode.argtypes = [l, p, p, p, l]
             L.orc_rans_decode.argtypes = [p, l, l, p, p]
@@ -188,6 +194,26 @@ def batch_bits_parallel(cfg, w, imgs, patch, n_proc=None, units=None):
     with mp.get_context("spawn").Pool(min(n_proc, max(1, len(tasks)))) as pool:
         parts = pool.map(_bits_task, tasks, chunksize=1)
     return float(sum(parts)), sum(t[2].shape[0] * t[2].shape[1] for t in tasks)
+
+
+def splitmix64(seed, k):
+    """Output k (0, 1, ...) of SplitMix64 seeded with seed."""
+    return int(lib().orc_splitmix64(int(seed) & (2 ** 64 - 1), int(k)))
+
+
+def sample_u16(seed, n, y, x, c):
+    """The sampler's uniform 16-bit value of channel c of pixel (y, x) of image n."""
+    return int(lib().orc_sample_u16(int(seed) & (2 ** 64 - 1), n, y, x, c))
+
+
+def sample_image(cfg, w, H, W, patch=0, seed=0, n=0):
+    """Image n of a batch drawn from the model in raster order (H, W, 3 uint8)."""
+    h, C_, R, K = cfg
+    img = np.zeros((H, W, 3), dtype=np.uint8)
+    w = _w64(w)
+    lib().orc_sample_image(h, C_, R, K, _ptr(w), H, W, patch, int(seed) & (2 ** 64 - 1), n,
+                           _ptr(img))
+    return img
 
 
 def rans_encode(start, freq):

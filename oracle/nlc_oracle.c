@@ -646,6 +646,77 @@ int orc_decode_image(int h, int C, int R, int K, const double *w, const uint8_t 
 }
 
 /* ------------------------------------------------------------------ */
+/* Sampling from the model (Section 5 names sampling as another use of  */
+/* the parallel schedules).  Counter-based uniforms: output k of the     */
+/* SplitMix64 generator (Steele, Lea and Flood, 2014) seeded with s is    */
+/* the finaliser applied to s + (k+1) gamma, gamma = 0x9E3779B97F4A7C15:  */
+/*   z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;                 */
+/*   z *= 0x94D049BB133111EB; z ^= z >> 31.                               */
+/* ------------------------------------------------------------------ */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Uniform 16-bit value of channel c of pixel (y, x) of image n. */
+uint32_t orc_sample_u16(uint64_t seed, int n, int y, int x, int c)
+{
+    uint64_t k = (((uint64_t)n << 21) + (uint64_t)y) << 21;
+    k = (k + (uint64_t)x) * 3 + (uint64_t)c;
+    return (uint32_t)(orc_splitmix64(seed, k) >> 48);
+}
+
+/* The symbol v with cum[v] <= u < cum[v+1] (inverse CDF of the table). */
+static int table_symbol(const uint32_t *cum, uint32_t u)
+{
+    int v = 0;
+    while (v < 255 && cum[v + 1] <= u) v++;
+    return v;
+}
+
+/* Draws image n of a batch in raster order over each unit: every channel
+ * is sampled from its quantised coding table with the uniform of
+ * orc_sample_u16. */
+void orc_sample_image(int h, int C, int R, int K, const double *w, int H, int W, int patch,
+                      uint64_t seed, int n, uint8_t *img)
+{
+    orc_cfg cfg = {h, C, R, K};
+    orc_w Wt;
+    orc_act A;
+    split_weights(&cfg, w, &Wt);
+    act_alloc(&cfg, &A);
+    memset(img, 0, (size_t)H * W * 3);
+    int nu = orc_num_units(H, W, patch);
+    uint32_t cum[257];
+    for (int u = 0; u < nu; u++) {
+        int y0, x0, Hu, Wu;
+        unit_of(H, W, patch, u, &y0, &x0, &Hu, &Wu);
+        for (int i = 0; i < Hu; i++)
+            for (int j = 0; j < Wu; j++) {
+                int y = y0 + i, x = x0 + j;
+                uint8_t *px = img + ((long)y * W + x) * 3;
+                orc_mix M;
+                gather_context(h, img, W, y0, x0, Hu, Wu, i, j, A.x);
+                forward_px(&cfg, &Wt, &A);
+                mix_from_params(K, A.out, 0, 0, &M);
+                channel_table(&M, 0, 0, 0, cum);
+                int r = table_symbol(cum, orc_sample_u16(seed, n, y, x, 0));
+                mix_from_params(K, A.out, r, 0, &M);
+                channel_table(&M, 1, r, 0, cum);
+                int g = table_symbol(cum, orc_sample_u16(seed, n, y, x, 1));
+                mix_from_params(K, A.out, r, g, &M);
+                channel_table(&M, 2, r, g, cum);
+                int b = table_symbol(cum, orc_sample_u16(seed, n, y, x, 2));
+                px[0] = (uint8_t)r; px[1] = (uint8_t)g; px[2] = (uint8_t)b;
+            }
+    }
+    act_free(&A);
+}
+
+/* ------------------------------------------------------------------ */
 /* Training objective (Eq. 2) in bits per dimension and its gradient.   */
 /* loss = (1 / (3 N H W)) sum_pixels -log2 p(pixel); each image is one  */
 /* unit (crops).                                                        */

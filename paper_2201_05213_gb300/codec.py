@@ -67,6 +67,15 @@ class Codec:
             self.check(stream)
         return outs
 
+    def sample(self, sizes, patch=0, seed=0, schedule=N.NLC_SCHED_WAVEFRONT, stream=None,
+               outs=None):
+        """Images of the given sizes drawn from the model (nlc_sample)."""
+        if outs is None:
+            outs = [torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for H, W in sizes]
+        N.nlc_sample(self.ctx, outs, patch, seed, schedule, stream)
+        self.check(stream)
+        return outs
+
     def plan(self, sizes, patch=0, layout=1, schedule=N.NLC_SCHED_WAVEFRONT, outs=None):
         """A DecodePlan for a fixed batch of image sizes."""
         return DecodePlan(self, sizes, patch, layout, schedule, outs)

@@ -52,7 +52,8 @@ struct nlc_ctx {
   float* d_grad = nullptr;
   float* d_loss = nullptr;
   long long adam_t = 0;
-  bool dirty = true;
+  bool dirty = true;       // packed weight copies out of date
+  bool hash_dirty = true;  // content hash out of date
   unsigned char* ws = nullptr;
   size_t ws_cap = 0;
   int px_per_cta = 8;
@@ -108,10 +109,19 @@ static DeviceModel model_view(const nlc_ctx* x) {
   return m;
 }
 
-static int ensure_packed(nlc_ctx* x, cudaStream_t s) {
-  if (!x->dirty) return NLC_OK;
-  CUDA_TRY(launch_repack(x->d, x->d_w, x->d_simt, x->d_umma, x->d_bias, x->d_hash, (int)x->n_w, s));
-  x->dirty = false;
+// Brings the packed weight copies (and, with hash, the content hash that the
+// containers carry) up to date.  Training steps skip the hash: only the
+// codec calls need it.
+static int ensure_packed(nlc_ctx* x, cudaStream_t s, bool hash = true) {
+  if (x->dirty) {
+    CUDA_TRY(launch_repack(x->d, x->d_w, x->d_simt, x->d_umma, x->d_bias, nullptr, (int)x->n_w, s));
+    x->dirty = false;
+    x->hash_dirty = true;
+  }
+  if (hash && x->hash_dirty) {
+    CUDA_TRY(launch_hash(x->d, x->d_w, (int)x->n_w, x->d_hash, s));
+    x->hash_dirty = false;
+  }
   return NLC_OK;
 }
 
@@ -548,6 +558,48 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   return NLC_OK;
 }
 
+extern "C" int nlc_sample(nlc_ctx* x, const nlc_image_out* outs, int n, int patch,
+                          uint64_t seed, int schedule, nlc_stream stream) {
+  if (!x || n < 0 || (n > 0 && !outs)) return fail(NLC_ERR_ARG, "bad arguments");
+  if (schedule < 0 || schedule > 2) return fail(NLC_ERR_ARG, "unknown schedule %d", schedule);
+  std::vector<int32_t> H(n), W(n);
+  std::vector<const void*> data(n);
+  std::vector<uint8_t*> ptrs(n);
+  for (int i = 0; i < n; i++) {
+    H[i] = outs[i].H;
+    W[i] = outs[i].W;
+    data[i] = outs[i].data;
+    ptrs[i] = outs[i].data;
+  }
+  int rc = check_images(n, H.data(), W.data(), data.data(), patch);
+  if (rc) return rc;
+  for (int i = 0; i < n; i++)
+    if (H[i] >= (1 << 21) || W[i] >= (1 << 21) || i >= (1 << 21))
+      return fail(NLC_ERR_UNSUPPORTED, "the sampler's counter needs sides and n below 2^21");
+  Batch b;
+  rc = plan_batch(x->d, n, ptrs.data(), H.data(), W.data(), patch, NLC_LAYOUT_ROW, schedule, b);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const DeviceModel m = model_view(x);
+  if (decode_smem_bytes(x->d, (int)b.units.size()) > 227 * 1024)
+    return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
+  CodecBufs cb;
+  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false);
+  if ((rc = ensure_ws(x, need))) return rc;
+  layout_bufs(b, x->ws, cb, x->d_status, false);
+  if ((rc = ensure_packed(x, s))) return rc;
+  if ((rc = upload_batch(b, cb, s))) return rc;
+  int gmax = decode_max_grid(m, (int)b.units.size(), x->sm_count, true);
+  if (gmax < 1) return fail(NLC_ERR_UNSUPPORTED, "sampler does not fit on an SM");
+  if (x->max_ctas > 0) gmax = std::min(gmax, x->max_ctas);
+  long long g = (b.max_front + x->px_per_cta - 1) / x->px_per_cta;
+  int grid = (int)std::max(1LL, std::min<long long>(g, gmax));
+  if ((long long)grid * b.T >= (1LL << 31) - 1) grid = 1;
+  const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
+  CUDA_TRY(launch_sample(m, cb, sched, (int)b.T, grid, (unsigned long long)seed, s));
+  return NLC_OK;
+}
+
 extern "C" int nlc_forward(nlc_ctx* x, const nlc_image_in* imgs, int n, int patch, float* d_params,
                            float* d_bits, nlc_stream stream) {
   if (!x || n < 0 || (n > 0 && !imgs)) return fail(NLC_ERR_ARG, "bad arguments");
@@ -620,11 +672,13 @@ static int run_adjoint(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W,
   const long long npx = (long long)N * H * W;
   if (npx > (1LL << 31) / 16) return fail(NLC_ERR_UNSUPPORTED, "batch too large");
   const bool tc = x->d.prec == NLC_BF16 && tc_train_fits(x->d);
+  if (!tc && !simt_train_fits(x->d))
+    return fail(NLC_ERR_UNSUPPORTED, "model too large for the training kernels' shared memory");
   const size_t need = tc ? tc_train_ws_bytes(x->d, npx, x->sm_count)
                          : train_ws_bytes(x->d, npx, x->sm_count);
   int rc = ensure_ws(x, need);
   if (rc) return rc;
-  if ((rc = ensure_packed(x, s))) return rc;
+  if ((rc = ensure_packed(x, s, false))) return rc;
   if (tc)
     CUDA_TRY(launch_tc_train(x->d, x->d_umma, x->d_bias, d_batch, N, H, W, d_dparams, d_loss,
                              d_grad, x->ws, x->sm_count, x->d_status, s));

@@ -162,6 +162,12 @@ cudaError_t launch_repack(const Dims& d, const float* w, float* simt, uint16_t* 
     e = launch_repack_umma(d, w, umma, bias, s);
     if (e != cudaSuccess) return e;
   }
+  if (hash == nullptr) return cudaSuccess;
+  return launch_hash(d, w, n_w, hash, s);
+}
+
+cudaError_t launch_hash(const Dims& d, const float* w, int n_w, unsigned long long* hash,
+                        cudaStream_t s) {
   hash_kernel<<<1, kThreads, 0, s>>>(d, w, n_w, hash);
   return cudaGetLastError();
 }

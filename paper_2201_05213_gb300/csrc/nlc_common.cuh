@@ -95,6 +95,26 @@ __device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) {
   asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", 2014): the k-th output (k = 0, 1, ...) of the generator seeded
+// with `seed` is the mixing function applied to seed + (k + 1) * gamma,
+// gamma = 0x9E3779B97F4A7C15.  Used as a counter-based generator: the
+// sampler's uniform 16-bit value of channel c of pixel (y, x) of image n is
+// the top 16 bits of output k = ((n * 2^21 + y) * 2^21 + x) * 3 + c.
+__host__ __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                                     unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint32_t sample_u16(unsigned long long seed, int image, int y,
+                                                        int x, int c) {
+  const unsigned long long k =
+      ((((unsigned long long)image << 21) + (unsigned long long)y) << 21) + (unsigned long long)x;
+  return (uint32_t)(splitmix64_at(seed, 3ull * k + (unsigned long long)c) >> 48);
+}
+
 // The GPU's global nanosecond timer.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -23,6 +23,7 @@ struct DecodeArgs {
   unsigned long long* prof;  // optional per-phase cycle counters
   unsigned long long* times;  // optional: [0] start, [t + 1] end of step t (ns)
   long long n_times;
+  unsigned long long seed;    // sampler only
 };
 
 // Threads of the decoder's CTA: the BF16 pipeline runs 16 warps (32 coding
@@ -121,7 +122,47 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
   }
 }
 
-template <int PREC>
+// Draws the tile's pixels from the model (Section 5: the parallel schedules
+// apply to sampling from a local autoregressive model): the symbol of each
+// channel is the one whose quantised interval [cum_v, cum_{v+1}) holds a
+// uniform 16-bit value from the counter-based generator (inverse-CDF
+// sampling of the coder's own table), found by the decoder's search.
+template <int GW, int NW>
+__device__ __noinline__ void sample_tile(const DecodeArgs& a, const TileSmem& t, int n) {
+  constexpr int gpw = 32 / GW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / GW, gl = lane % GW;
+  const int K = a.m.d.K;
+  for (int j = 0; gpw * warp + NW * gpw * j < n; j++) {
+    const int s = gpw * warp + grp + NW * gpw * j;
+    const bool valid = s < n;
+    const int se = valid ? s : s - 1;  // an idle group shadows its neighbour
+    const PixSlot ps = t.slots[se];
+    const Unit U = a.units[ps.unit];
+    const int y = U.y0 + ps.i, x = U.x0 + ps.j;
+    WarpScratch& ws = t.ws[gpw * warp + grp];
+    CompState cs;
+    comp_init<GW>(tile_params(t, a.m.d, se), K, gl, cs);
+    int v[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ch++) {
+      int nact;
+      const float mloc = channel_setup<GW>(cs, K, ch, v[0], v[1], gl, ws, nact);
+      const uint32_t u = sample_u16(a.seed, U.image, y, x, ch);
+      uint32_t lo, hi;
+      v[ch] = cdf_search<GW>(ws, nact, u, gl, lo, hi);
+      if (ch < 2) comp_observe(cs, K, ch, mloc, v[ch], gl);
+      __syncwarp();
+    }
+    if (gl == 0 && valid) {
+      uint8_t* px = U.img + ((long long)y * U.img_W + x) * 3;
+      px[0] = (uint8_t)v[0];
+      px[1] = (uint8_t)v[1];
+      px[2] = (uint8_t)v[2];
+    }
+  }
+}
+
+template <int PREC, bool SAMPLE>
 __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(DecodeArgs a) {
   constexpr int NT = decode_threads<PREC>(), NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -204,7 +245,7 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       // record's pos + 8, read only when the pixel is done.
       const bool wide = n <= NW;
       const int sl = wide ? group_slot<32, NW>(warp, lane) : group_slot<kGW, NW>(warp, lane);
-      if (sl < n) {
+      if (!SAMPLE && sl < n) {
         const StreamRec* r = a.st + t.slots[sl].aux;
         cp_async16(t.rec + sl, r);
         cp_async16(&t.rec[sl].pos, &r->pos);
@@ -212,6 +253,13 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       if (pr) pc[5] += 1;
       tick(1);
       tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+      if constexpr (SAMPLE) {
+        if (wide) sample_tile<32, NW>(a, t, n);
+        else sample_tile<kGW, NW>(a, t, n);
+        __syncthreads();
+        tick(3);
+        continue;
+      }
       cp_async_wait_all();
       if (sl < n) {
         const unsigned long long w0 = (t.rec[sl].pos + 8ull) & ~3ull, end = t.rec[sl].end;
@@ -271,14 +319,17 @@ size_t decode_smem_bytes(const Dims& d, int n_units) {
   return tile_smem_bytes(d, n_units, decode_threads_of(d.prec) / kGW, true);
 }
 
-static const void* decode_fn(int prec) {
-  return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16>
-                           : (const void*)decode_kernel<PREC_FP32>;
+static const void* decode_fn(int prec, bool sample = false) {
+  if (sample)
+    return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16, true>
+                             : (const void*)decode_kernel<PREC_FP32, true>;
+  return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16, false>
+                           : (const void*)decode_kernel<PREC_FP32, false>;
 }
 
-int decode_max_grid(const DeviceModel& m, int n_units, int sm_count) {
+int decode_max_grid(const DeviceModel& m, int n_units, int sm_count, bool sample) {
   const size_t smem = decode_smem_bytes(m.d, n_units);
-  const void* fn = decode_fn(m.d.prec);
+  const void* fn = decode_fn(m.d.prec, sample);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -321,6 +372,38 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   if (set_attr &&
       (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
           cudaSuccess)
+    return e;
+  a.seed = 0;
+  void* args[] = {&a};
+  if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(nt), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(1), dim3(nt), args, smem, s);
+}
+
+cudaError_t launch_sample(const DeviceModel& m, const CodecBufs& b, int sched, int T, int grid,
+                          unsigned long long seed, cudaStream_t s) {
+  cudaError_t e;
+  if (b.n_units == 0) return cudaSuccess;
+  if ((e = cudaMemsetAsync(b.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+  DecodeArgs a;
+  a.m = m;
+  a.units = b.units;
+  a.n_units = b.n_units;
+  a.layout = 1;
+  a.sched = sched;
+  a.T = T;
+  a.in = nullptr;
+  a.st = nullptr;
+  a.bar = b.bar;
+  a.status = b.status;
+  a.prof = nullptr;
+  a.times = nullptr;
+  a.n_times = 0;
+  a.seed = seed;
+  const size_t smem = decode_smem_bytes(m.d, b.n_units);
+  const void* fn = decode_fn(m.d.prec, true);
+  const int nt = decode_threads_of(m.d.prec);
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
     return e;
   void* args[] = {&a};
   if (grid > 1) return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(nt), args, smem, s);

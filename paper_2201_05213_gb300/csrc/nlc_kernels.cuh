@@ -63,8 +63,11 @@ struct CodecBufs {
 };
 
 // Launchers (return cudaError_t of the launch).
+// hash == nullptr: the packed copies only (the content hash is left as is)
 cudaError_t launch_repack(const Dims& d, const float* w, float* simt, uint16_t* umma, float* bias,
                           unsigned long long* hash, int n_w, cudaStream_t s);
+cudaError_t launch_hash(const Dims& d, const float* w, int n_w, unsigned long long* hash,
+                        cudaStream_t s);
 
 cudaError_t launch_encode(const DeviceModel& m, const CodecBufs& b, int layout, int patch,
                           uint8_t* out, unsigned long long cap, unsigned long long* d_offsets,
@@ -79,7 +82,11 @@ cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t
 cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
                           const unsigned long long* d_offsets, int layout, int patch, int sched,
                           int T, int grid, cudaStream_t s, bool set_attr = true);
-int decode_max_grid(const DeviceModel& m, int n_units, int sm_count);
+int decode_max_grid(const DeviceModel& m, int n_units, int sm_count, bool sample = false);
+// The decoder's schedule and tables driven by a counter-based generator
+// instead of streams: draws the batch's pixels from the model.
+cudaError_t launch_sample(const DeviceModel& m, const CodecBufs& b, int sched, int T, int grid,
+                          unsigned long long seed, cudaStream_t s);
 size_t decode_smem_bytes(const Dims& d, int n_units);
 cudaError_t launch_forward(const DeviceModel& m, const CodecBufs& b, float* params, float* bits,
                            int sm_count, cudaStream_t s);

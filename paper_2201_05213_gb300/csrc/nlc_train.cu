@@ -333,12 +333,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 __global__ void reduce_grad_kernel(const float* __restrict__ part_g, const float* __restrict__ part_l,
-                                   int nblk, int n_w, float inv_dims, float* __restrict__ grad,
-                                   float* __restrict__ loss) {
+                                   int nblk, int n_w, int ldw, float inv_dims,
+                                   float* __restrict__ grad, float* __restrict__ loss) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_w) {
     float s = 0.f;
-    for (int b = 0; b < nblk; b++) s = __fadd_rn(s, part_g[(size_t)b * n_w + i]);
+    for (int b = 0; b < nblk; b++) s = __fadd_rn(s, part_g[(size_t)b * ldw + i]);
     grad[i] = s;
   }
   if (i == 0 && part_l && loss) {
@@ -348,13 +348,15 @@ __global__ void reduce_grad_kernel(const float* __restrict__ part_g, const float
   }
 }
 
-cudaError_t launch_reduce_grad(const float* part_g, const float* part_l, int nblk, int n_w,
+cudaError_t launch_reduce_grad(const float* part_g, const float* part_l, int nblk, int n_w, int ldw,
                                long long n_px, float* grad, float* loss, cudaStream_t s) {
   const float inv_dims = 1.f / (0.6931471805599453f * 3.f * (float)n_px);
-  reduce_grad_kernel<<<(n_w + 255) / 256, 256, 0, s>>>(part_g, part_l, nblk, n_w, inv_dims, grad,
-                                                      loss);
+  reduce_grad_kernel<<<(n_w + 255) / 256, 256, 0, s>>>(part_g, part_l, nblk, n_w, ldw, inv_dims,
+                                                      grad, loss);
   return cudaGetLastError();
 }
+
+bool simt_train_fits(const Dims& d) { return train_smem_bytes(d) <= 227 * 1024; }
 
 static int train_grid(long long n_px, int sm_count) {
   long long t = (n_px + kTM - 1) / kTM;
@@ -385,7 +387,7 @@ cudaError_t launch_loss_grad(const Dims& d, const float* w, const float* wt, con
   loss_grad_kernel<<<g, kThreads, smem, s>>>(d, w, wt, batch, N, H, W, dparams, part_g, part_l,
                                               n_w);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return launch_reduce_grad(part_g, dparams ? nullptr : part_l, g, n_w, n_px, grad, loss, s);
+  return launch_reduce_grad(part_g, dparams ? nullptr : part_l, g, n_w, n_w, n_px, grad, loss, s);
 }
 
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,

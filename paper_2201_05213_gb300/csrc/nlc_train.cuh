@@ -18,8 +18,10 @@ cudaError_t launch_loss_grad(const Dims& d, const float* w, const float* wt, con
                              void* ws, int sm_count, cudaStream_t s);
 // Sums per-CTA gradient slots (and loss partials, if part_l and loss are
 // non-null) in a fixed order.
-cudaError_t launch_reduce_grad(const float* part_g, const float* part_l, int nblk, int n_w,
+cudaError_t launch_reduce_grad(const float* part_g, const float* part_l, int nblk, int n_w, int ldw,
                                long long n_px, float* grad, float* loss, cudaStream_t s);
+// Whether the FP32 SIMT training kernel's tiles fit in one CTA.
+bool simt_train_fits(const Dims& d);
 // BF16 tensor-core path (tcgen05), same contract; fits: whether the model's
 // tiles fit in one CTA's shared memory.
 bool tc_train_fits(const Dims& d);

@@ -40,6 +40,7 @@ EXPORTS = [
     "nlc_compress_noalloc", "nlc_decode_profile",
     "nlc_plan_decode", "nlc_plan_run", "nlc_plan_tune", "nlc_plan_destroy",
     "nlc_decode_step_times", "nlc_measure_mufu", "nlc_backward", "nlc_load_weights",
+    "nlc_sample",
 ]
 
 
@@ -101,6 +102,7 @@ def load():
             L.nlc_measure_mufu.argtypes = [i, p, p, p]
             L.nlc_backward.argtypes = [p, p, i, i, i, p, p, p]
             L.nlc_load_weights.argtypes = [p, p, sz, p]
+            L.nlc_sample.argtypes = [p, p, i, i, C.c_uint64, i, p]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -319,3 +321,10 @@ def nlc_backward(ctx, batch, dparams, dweights, stream=None):
 def nlc_load_weights(ctx, weights, stream=None):
     """Weights from a device FP32 tensor (asynchronous)."""
     _check(load().nlc_load_weights(ctx, _ptr(weights), int(weights.numel()), _stream(stream)))
+
+
+def nlc_sample(ctx, outs, patch, seed, schedule, stream=None):
+    """Draws len(outs) images from the model into the uint8 CUDA tensors outs."""
+    arr, n = _images(outs), len(outs)
+    _check(load().nlc_sample(ctx, arr, n, patch, int(seed) & 0xFFFFFFFFFFFFFFFF, schedule,
+                             _stream(stream)))
