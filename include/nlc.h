@@ -65,7 +65,13 @@ typedef enum {
   NLC_ERR_UNSUPPORTED = 7  /* configuration outside the compiled limits     */
 } nlc_status;
 
-typedef enum { NLC_FP32 = 0, NLC_BF16 = 1 } nlc_precision;
+/* Network arithmetic.  NLC_BF16_SHEARED is the BF16 network with its first
+ * layer evaluated as Section 3.1's sheared kernels (Fig. 5) over the h+1 rows
+ * of the h(h+2) sheared columns before the pixel (ShearLoC): the same model
+ * function, rounded differently, so its containers are its own; its
+ * wavefront decoder keeps the decoded pixels in a sheared layout and reads
+ * each front's context as one rectangular window. */
+typedef enum { NLC_FP32 = 0, NLC_BF16 = 1, NLC_BF16_SHEARED = 2 } nlc_precision;
 
 /* Decode schedules.  All three decode the same container to the same pixels
  * (Section 4: every schedule has the same compression rate). */

@@ -73,7 +73,8 @@ static bool cfg_ok(const nlc_model_cfg* c) {
   return c && c->h >= 1 && c->h <= kMaxH && (c->C == 16 || c->C == 32 || c->C == 48 ||
                                                c->C == 64) &&
          c->n_res >= 0 && c->n_res <= kMaxR && c->K >= 1 && c->K <= kMaxK &&
-         (c->precision == NLC_FP32 || c->precision == NLC_BF16);
+         (c->precision == NLC_FP32 || c->precision == NLC_BF16 ||
+          c->precision == NLC_BF16_SHEARED);
 }
 
 static Dims make_dims(const nlc_model_cfg* c) {
@@ -87,7 +88,10 @@ static Dims make_dims(const nlc_model_cfg* c) {
   d.NO = 10 * c->K;
   d.NOp = (d.NO + 15) / 16 * 16;
   d.ldP = d.NOp + 1;  // odd: one pixel per lane stores its row without bank conflicts
-  d.prec = c->precision;
+  d.shear = c->precision == NLC_BF16_SHEARED ? 1 : 0;
+  d.prec = d.shear ? NLC_BF16 : c->precision;
+  d.Ws = c->h * (c->h + 2);
+  d.Fsp = (3 * d.Ws + 15) / 16 * 16;
   return d;
 }
 
@@ -172,7 +176,7 @@ extern "C" int nlc_create(const nlc_model_cfg* cfg, const float* h_w, size_t n, 
   if (!cfg_ok(cfg))
     return fail(NLC_ERR_UNSUPPORTED,
                 "unsupported configuration (h 1..3, C in {16,32,48,64}, n_res 0..4, K 1..16, "
-                "precision 0/1)");
+                "precision 0/1/2)");
   if (!h_w || n != nlc_num_weights(cfg))
     return fail(NLC_ERR_ARG, "expected %zu weights, got %zu", nlc_num_weights(cfg), n);
   nlc_ctx* x = new nlc_ctx();
@@ -314,6 +318,7 @@ struct Batch {
   int n_streams = 0;
   long long T = 0;        // decode steps
   long long max_front = 0;
+  long long ring_rows = 0;  // rows of all units (the sheared decoder's ring)
 };
 
 static int plan_batch(const Dims& d, int n, uint8_t* const* ptrs, const int32_t* H,
@@ -325,6 +330,7 @@ static int plan_batch(const Dims& d, int n, uint8_t* const* ptrs, const int32_t*
   b.T = 0;
   b.max_front = 0;
   const int o = d.h + 1;
+  int ring_rows = 0;
   for (int i = 0; i < n; i++) {
     const long long img_px_base = b.n_px;
     ImageRec I;
@@ -349,7 +355,8 @@ static int plan_batch(const Dims& d, int n, uint8_t* const* ptrs, const int32_t*
           u.Wu = std::min(P, W[i] - xx);
           u.stream_base = b.n_streams;
           u.image = i;
-          u.pad_ = 0;
+          u.ring_row = ring_rows;
+          ring_rows += u.Hu;
           u.img_px_base = img_px_base;
           long long Tu;
           if (sched_mode == NLC_SCHED_WAVEFRONT) {
@@ -377,6 +384,7 @@ static int plan_batch(const Dims& d, int n, uint8_t* const* ptrs, const int32_t*
     I.n_streams = b.n_streams - I.stream_base;
     b.images.push_back(I);
   }
+  b.ring_rows = ring_rows;
   if (b.T > INT32_MAX || b.n_px > (1LL << 40))
     return fail(NLC_ERR_UNSUPPORTED, "batch too large");
   return NLC_OK;
@@ -421,7 +429,7 @@ static int ensure_ws(nlc_ctx* x, size_t bytes) {
 
 // Lays out the per-call buffers; with base == nullptr only measures.
 static size_t layout_bufs(const Batch& b, unsigned char* base, CodecBufs& cb, int* status,
-                          bool encode) {
+                          bool encode, bool ring = false) {
   Arena a{base};
   const size_t U = b.units.size(), S = (size_t)b.n_streams;
   cb.units = a.take<Unit>(U + 1);
@@ -443,6 +451,7 @@ static size_t layout_bufs(const Batch& b, unsigned char* base, CodecBufs& cb, in
     cb.stage = nullptr;
     cb.scratch = nullptr;
   }
+  cb.ring = ring ? a.take<uint8_t>((size_t)kRingRowBytes * (size_t)(b.ring_rows + 1)) : nullptr;
   cb.status = status;
   return a.off;
 }
@@ -537,12 +546,13 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   if (decode_smem_bytes(x->d, (int)b.units.size()) > 227 * 1024)
     return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
   CodecBufs cb;
-  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false);
+  const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
+  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false, ring);
   if ((rc = ensure_ws(x, need))) return rc;
-  layout_bufs(b, x->ws, cb, x->d_status, false);
+  layout_bufs(b, x->ws, cb, x->d_status, false, ring);
   if ((rc = ensure_packed(x, s))) return rc;
   if ((rc = upload_batch(b, cb, s))) return rc;
-  int gmax = decode_max_grid(m, (int)b.units.size(), x->sm_count);
+  int gmax = decode_max_grid(m, (int)b.units.size(), x->sm_count, false, ring);
   if (gmax < 1) return fail(NLC_ERR_UNSUPPORTED, "decoder does not fit on an SM");
   if (x->max_ctas > 0) gmax = std::min(gmax, x->max_ctas);
   long long g = (b.max_front + x->px_per_cta - 1) / x->px_per_cta;
@@ -584,12 +594,13 @@ extern "C" int nlc_sample(nlc_ctx* x, const nlc_image_out* outs, int n, int patc
   if (decode_smem_bytes(x->d, (int)b.units.size()) > 227 * 1024)
     return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
   CodecBufs cb;
-  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false);
+  const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
+  size_t need = layout_bufs(b, nullptr, cb, x->d_status, false, ring);
   if ((rc = ensure_ws(x, need))) return rc;
-  layout_bufs(b, x->ws, cb, x->d_status, false);
+  layout_bufs(b, x->ws, cb, x->d_status, false, ring);
   if ((rc = ensure_packed(x, s))) return rc;
   if ((rc = upload_batch(b, cb, s))) return rc;
-  int gmax = decode_max_grid(m, (int)b.units.size(), x->sm_count, true);
+  int gmax = decode_max_grid(m, (int)b.units.size(), x->sm_count, true, ring);
   if (gmax < 1) return fail(NLC_ERR_UNSUPPORTED, "sampler does not fit on an SM");
   if (x->max_ctas > 0) gmax = std::min(gmax, x->max_ctas);
   long long g = (b.max_front + x->px_per_cta - 1) / x->px_per_cta;
@@ -671,7 +682,7 @@ static int run_adjoint(nlc_ctx* x, const uint8_t* d_batch, int N, int H, int W,
                        const float* d_dparams, float* d_loss, float* d_grad, cudaStream_t s) {
   const long long npx = (long long)N * H * W;
   if (npx > (1LL << 31) / 16) return fail(NLC_ERR_UNSUPPORTED, "batch too large");
-  const bool tc = x->d.prec == NLC_BF16 && tc_train_fits(x->d);
+  const bool tc = x->d.prec == NLC_BF16 && tc_train_fits(x->d);  // sheared: the same weights
   if (!tc && !simt_train_fits(x->d))
     return fail(NLC_ERR_UNSUPPORTED, "model too large for the training kernels' shared memory");
   const size_t need = tc ? tc_train_ws_bytes(x->d, npx, x->sm_count)
@@ -858,13 +869,14 @@ extern "C" int nlc_plan_decode(nlc_ctx* x, const nlc_image_out* outs, int n, int
   p->max_front = b.max_front;
   p->n_units = (int)b.units.size();
   p->px_per_cta = x->px_per_cta;
-  const size_t need = layout_bufs(b, nullptr, p->cb, x->d_status, false);
+  const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
+  const size_t need = layout_bufs(b, nullptr, p->cb, x->d_status, false, ring);
   cudaError_t e = cudaMalloc((void**)&p->d_buf, std::max<size_t>(need, 256));
   if (e != cudaSuccess) {
     delete p;
     return fail(NLC_ERR_CUDA, "cudaMalloc failed: %s", cudaGetErrorString(e));
   }
-  layout_bufs(b, p->d_buf, p->cb, x->d_status, false);
+  layout_bufs(b, p->d_buf, p->cb, x->d_status, false, ring);
   if (!b.units.empty())
     e = cudaMemcpy((void*)p->cb.units, b.units.data(), b.units.size() * sizeof(Unit),
                    cudaMemcpyHostToDevice);
@@ -877,7 +889,7 @@ extern "C" int nlc_plan_decode(nlc_ctx* x, const nlc_image_out* outs, int n, int
     return fail(NLC_ERR_CUDA, "unit table upload failed: %s", cudaGetErrorString(e));
   }
   // sets the decoder's shared-memory attribute for this batch, so runs need not
-  p->gmax = decode_max_grid(model_view(x), p->n_units, x->sm_count);
+  p->gmax = decode_max_grid(model_view(x), p->n_units, x->sm_count, false, ring);
   if (p->gmax < 1) {
     cudaFree(p->d_buf);
     delete p;

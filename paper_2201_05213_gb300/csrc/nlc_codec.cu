@@ -78,7 +78,7 @@ __global__ void hash_kernel(Dims d, const float* __restrict__ w, int n, unsigned
   if (threadIdx.x == 0) {
     unsigned long long t = mix64(((unsigned long long)d.h << 48) ^ ((unsigned long long)d.C << 32) ^
                                  ((unsigned long long)d.R << 16) ^ (unsigned long long)d.K);
-    t ^= mix64(0xABCDull ^ (unsigned long long)d.prec);
+    t ^= mix64(0xABCDull ^ (unsigned long long)prec_code(d));
     for (int i = 0; i < (int)blockDim.x; i++) t ^= part[i];
     *out = t;
   }
@@ -96,8 +96,15 @@ __global__ void repack_umma_kernel(Dims d, const float* __restrict__ w, uint16_t
     long long o = e;
     int Kd;
     long long wbase;  // canonical offset of the FP32 matrix
-    int kind;         // 0 W0, 1 hidden, 2 head
-    if (o < (long long)C * Fp) {
+    int kind;         // 0 W0, 1 hidden, 2 head, 3 sheared W0
+    int dd = 0;       // sheared: window row (0 = top, h = the pixel's own row)
+    const long long plain = (long long)umma_plain_halves(d);
+    if (o >= plain) {
+      o -= plain;
+      dd = (int)(o / ((long long)C * d.Fsp));
+      o %= (long long)C * d.Fsp;
+      Kd = d.Fsp; wbase = 0; kind = 3;
+    } else if (o < (long long)C * Fp) {
       Kd = Fp; wbase = 0; kind = 0;
     } else {
       o -= (long long)C * Fp;
@@ -121,7 +128,20 @@ __global__ void repack_umma_kernel(Dims d, const float* __restrict__ w, uint16_t
     const int r = rb * 8 + within / 8, k = kb * 8 + within % 8;
     float v;
     if (kind == 0) v = k < F ? __fdiv_rn(w[(long long)r * F + k], 255.f) : 0.f;
-    else if (kind == 1) v = w[wbase + (long long)r * C + k];
+    else if (kind == 3) {
+      // window row dd, window column q = k / 3 (channel k % 3): the pixel at
+      // row offset dy = dd - h and column offset dx = q - Ws + (h+1)(h - dd)
+      // (the sheared column t - Ws + q of row i + dy, t = j + (h+1) i); its
+      // weight is the tap's (Fig. 5), 0 where the window holds no tap
+      const int h = d.h, q = k / 3, c = k % 3;
+      const int dy = dd - h, dx = q - d.Ws + (h + 1) * (h - dd);
+      int p = -1;
+      if (k < 3 * d.Ws) {
+        if (dy < 0 && dx >= -h && dx <= h) p = (dy + h) * (2 * h + 1) + (dx + h);
+        if (dy == 0 && dx >= -h && dx <= -1) p = h * (2 * h + 1) + (dx + h);
+      }
+      v = p >= 0 ? __fdiv_rn(w[(long long)r * F + 3 * p + c], 255.f) : 0.f;
+    } else if (kind == 1) v = w[wbase + (long long)r * C + k];
     else v = r < NO ? w[wbase + (long long)r * C + k] : 0.f;
     umma[e] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
   }
@@ -279,7 +299,7 @@ __global__ void pack_copy_kernel(DeviceModel m, const Unit* __restrict__ units, 
     h[4] = (uint8_t)kVersion;
     h[5] = (uint8_t)m.d.h;
     h[6] = (uint8_t)layout;
-    h[7] = (uint8_t)m.d.prec;
+    h[7] = (uint8_t)prec_code(m.d);
     *reinterpret_cast<uint32_t*>(h + 8) = (uint32_t)I.H;
     *reinterpret_cast<uint32_t*>(h + 12) = (uint32_t)I.W;
     *reinterpret_cast<uint32_t*>(h + 16) = (uint32_t)patch;
@@ -309,7 +329,7 @@ __global__ void pack_empty_kernel(DeviceModel m, const ImageRec* __restrict__ im
   h[4] = (uint8_t)kVersion;
   h[5] = (uint8_t)m.d.h;
   h[6] = (uint8_t)layout;
-  h[7] = (uint8_t)m.d.prec;
+  h[7] = (uint8_t)prec_code(m.d);
   *reinterpret_cast<uint32_t*>(h + 8) = (uint32_t)I.H;
   *reinterpret_cast<uint32_t*>(h + 12) = (uint32_t)I.W;
   *reinterpret_cast<uint32_t*>(h + 16) = (uint32_t)patch;
@@ -369,7 +389,7 @@ __global__ void parse_header_kernel(DeviceModel m, const ImageRec* __restrict__ 
         *reinterpret_cast<const uint32_t*>(h + 16) != (uint32_t)patch ||
         *reinterpret_cast<const uint32_t*>(h + 20) != (uint32_t)I.n_streams)
       err = ST_CORRUPT;
-    else if (h[7] != m.d.prec || *reinterpret_cast<const unsigned long long*>(h + 24) != *m.hash)
+    else if (h[7] != prec_code(m.d) || *reinterpret_cast<const unsigned long long*>(h + 24) != *m.hash)
       err = ST_WEIGHTS;
   }
   bad[i] = err;

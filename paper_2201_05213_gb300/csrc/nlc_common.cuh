@@ -40,11 +40,20 @@ enum Schedule { SCHED_RASTER = 0, SCHED_WAVEFRONT = 1 };
 // Fp = F rounded up to a multiple of 16, NO = 10K network outputs, NOp = NO
 // rounded up to a multiple of 16, ldP = NOp + 1 (row stride of the per-pixel
 // outputs in shared memory; odd, against bank conflicts).
+// shear = 1: the first layer is evaluated as the sheared kernels of Section
+// 3.1 (Fig. 5) over the h+1 rows of the h(h+2) sheared columns before the
+// pixel's own (Ws = h(h+2) pixels, Fsp = 3 Ws rounded up to 16 features per
+// window row); the network runs in BF16 (prec = PREC_BF16).
 struct Dims {
   int h, C, R, K;
   int F, Fp, NO, NOp, ldP;
   int prec;
+  int shear, Ws, Fsp;
 };
+
+// Precision byte of a container (and of the model's hash): 0 FP32, 1 BF16,
+// 2 BF16 with the sheared first layer.
+__host__ __device__ __forceinline__ int prec_code(const Dims& d) { return d.shear ? 2 : d.prec; }
 
 // One coding unit (a whole image or one patch of it).
 struct Unit {
@@ -55,7 +64,7 @@ struct Unit {
   int stream_base;       // index of the unit's first rANS stream
   int start_step;        // global step at which the unit's local step 0 runs
   int image;             // image index in the batch
-  int pad_;
+  int ring_row;          // rows of all preceding units (the sheared decoder's ring rows)
   long long img_px_base; // pixels of all preceding images (raster output order)
 };
 

@@ -24,6 +24,7 @@ struct DecodeArgs {
   unsigned long long* times;  // optional: [0] start, [t + 1] end of step t (ns)
   long long n_times;
   unsigned long long seed;    // sampler only
+  uint8_t* ring;              // sheared wavefront decoder: the units' sheared rings
 };
 
 // Threads of the decoder's CTA: the BF16 pipeline runs 16 warps (32 coding
@@ -44,7 +45,20 @@ __device__ __forceinline__ int group_slot(int warp, int l) {
 // pixels' stream records are in t.rec (visible to the warp), their windows
 // are being copied to t.win by the warp's lanes.  With pc non-null, thread 0
 // accumulates its sub-stage cycles in pc[8..12].
-template <int GW, int NW>
+// Stores a decoded pixel of sheared column tau = j + (h+1) i in its unit's
+// ring row (twice, at slots tau mod 16 and tau mod 16 + 16).
+__device__ __forceinline__ void ring_put(const DecodeArgs& a, const Unit& U, int i, int j,
+                                         const int (&v)[3]) {
+  const int tau = j + (a.m.d.h + 1) * i;
+  uint8_t* r = a.ring + (long long)kRingRowBytes * (U.ring_row + i) + 3 * (tau & 15);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    r[c] = (uint8_t)v[c];
+    r[48 + c] = (uint8_t)v[c];
+  }
+}
+
+template <int GW, int NW, bool SHEAR>
 __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, int n,
                                        long long* pc) {
   constexpr int gpw = 32 / GW;
@@ -84,7 +98,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       ck = clock64();
       pc[12] += 1;
     }
-    comp_init<GW>(tile_params(t, a.m.d, se), K, gl, cs);
+    comp_init<GW>(tile_params(t, a.m.d, SHEAR ? t.prow[se] : se), K, gl, cs);
     int v[3] = {0, 0, 0};
     for (int ch = 0; ch < 3; ch++) {
       int nact;
@@ -109,6 +123,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       px[0] = (uint8_t)v[0];
       px[1] = (uint8_t)v[1];
       px[2] = (uint8_t)v[2];
+      if (SHEAR) ring_put(a, U, ps.i, ps.j, v);
       const int sid = ps.aux;
       const unsigned long long np = dec.pos + (unsigned long long)dec.used;
       uint32_t n0, n1;
@@ -127,7 +142,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
 // channel is the one whose quantised interval [cum_v, cum_{v+1}) holds a
 // uniform 16-bit value from the counter-based generator (inverse-CDF
 // sampling of the coder's own table), found by the decoder's search.
-template <int GW, int NW>
+template <int GW, int NW, bool SHEAR>
 __device__ __noinline__ void sample_tile(const DecodeArgs& a, const TileSmem& t, int n) {
   constexpr int gpw = 32 / GW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -142,7 +157,7 @@ __device__ __noinline__ void sample_tile(const DecodeArgs& a, const TileSmem& t,
     const int y = U.y0 + ps.i, x = U.x0 + ps.j;
     WarpScratch& ws = t.ws[gpw * warp + grp];
     CompState cs;
-    comp_init<GW>(tile_params(t, a.m.d, se), K, gl, cs);
+    comp_init<GW>(tile_params(t, a.m.d, SHEAR ? t.prow[se] : se), K, gl, cs);
     int v[3] = {0, 0, 0};
     for (int ch = 0; ch < 3; ch++) {
       int nact;
@@ -158,11 +173,17 @@ __device__ __noinline__ void sample_tile(const DecodeArgs& a, const TileSmem& t,
       px[0] = (uint8_t)v[0];
       px[1] = (uint8_t)v[1];
       px[2] = (uint8_t)v[2];
+      if (SHEAR) ring_put(a, U, ps.i, ps.j, v);
     }
   }
 }
 
-template <int PREC, bool SAMPLE>
+// SHEAR: the sheared model's wavefront decoder (Section 3.1): decoded pixels
+// also go to per-unit sheared rings, and each tile's context is one window
+// tile of (unit, row) rows read from the rings, every unit's piece of the
+// front preceded by h halo rows, with the first layer's MMAs reading the
+// window rows of output row m at rows m .. m + h.
+template <int PREC, bool SAMPLE, bool SHEAR>
 __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(DecodeArgs a) {
   constexpr int NT = decode_threads<PREC>(), NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -216,6 +237,47 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       t.slots[s] = ps;
     }
   };
+  // Sheared tile of at most nmax pixels from front position base: the
+  // pixels' slots, their output rows prow (pixel s of the tile's k-th unit
+  // piece at s + h k: each piece is preceded by h halo window rows), the
+  // window rows' (unit, unit row), and t.flag[1..3] = the tile's pixels,
+  // output rows and window rows (the output rows stay below MT).
+  auto fill_slots_shear = [&](int step, long long base, int nmax, int nt) {
+    fill_slots(step, base, nmax, nt);
+    for (int r = threadIdx.x; r < kWinRows; r += nt) t.wrow[r] = make_int2(-1, 0);
+    part_sync(nt);
+    if (threadIdx.x < MT) {  // warps 0 .. MT/32 - 1
+      const int s = threadIdx.x, w = s >> 5, l = s & 31;
+      const bool valid = s < nmax;
+      const bool start = valid && (s == 0 || t.slots[s].unit != t.slots[s - 1].unit);
+      const unsigned bal = __ballot_sync(0xffffffffu, start);
+      if (l == 0) t.sh[w] = __popc(bal);
+      asm volatile("bar.sync 2, %0;" ::"n"(MT) : "memory");
+      int before = 0;
+      for (int k = 0; k < w; k++) before += (int)t.sh[k];
+      const int seg = before + __popc(bal & (0xffffffffu >> (31 - l))) - 1;
+      const int pr = s + h * seg;
+      const bool fits = valid && pr < MT;
+      const unsigned fb = __ballot_sync(0xffffffffu, fits);
+      asm volatile("bar.sync 2, %0;" ::"n"(MT) : "memory");
+      if (l == 0) t.sh[w] = __popc(fb);
+      asm volatile("bar.sync 2, %0;" ::"n"(MT) : "memory");
+      const int n = (int)(t.sh[0] + t.sh[1] + t.sh[2] + t.sh[3]);
+      t.prow[s] = pr;
+      if (fits) {
+        const PixSlot ps = t.slots[s];
+        t.wrow[pr + h] = make_int2(ps.unit, ps.i);
+        if (start)
+          for (int k = 1; k <= h; k++)
+            t.wrow[pr + h - k] = make_int2(ps.i - k >= 0 ? ps.unit : -1, ps.i - k);
+      }
+      if (s == n - 1) {
+        t.flag[1] = n;
+        t.flag[2] = pr + 1;
+        t.flag[3] = pr + 1 + h;
+      }
+    }
+  };
   // The schedule of step t + 1 (front sizes, this CTA's share, its first
   // tile's slots) needs no decoded data, so it is computed between arriving
   // at the grid barrier after step t and waiting for the others: the last
@@ -226,16 +288,21 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   int F = front_scan(a.units, a.n_units, 0, h, a.sched, t.pre, t.sh, (int)blockDim.x);
   tick(0);
   long long lo = (long long)F * blockIdx.x / G, hi = (long long)F * (blockIdx.x + 1) / G;
-  if (lo < hi) fill_slots(0, lo, (int)min((long long)MT, hi - lo), (int)blockDim.x);
+  if (lo < hi) {
+    if constexpr (SHEAR) fill_slots_shear(0, lo, (int)min((long long)MT, hi - lo), (int)blockDim.x);
+    else fill_slots(0, lo, (int)min((long long)MT, hi - lo), (int)blockDim.x);
+  }
   __syncthreads();
   tick(1);
   for (int step = 0; step < a.T; step++) {
-    for (long long base = lo; base < hi; base += MT) {
-      const int n = (int)min((long long)MT, hi - base);
+    for (long long base = lo; base < hi;) {
+      int n = (int)min((long long)MT, hi - base);
       if (base != lo) {  // further tiles of a large share
-        fill_slots(step, base, n, (int)blockDim.x);
+        if constexpr (SHEAR) fill_slots_shear(step, base, n, (int)blockDim.x);
+        else fill_slots(step, base, n, (int)blockDim.x);
         __syncthreads();
       }
+      if constexpr (SHEAR) n = t.flag[1];
       // A CTA with at most one pixel per warp codes with whole warps (lower
       // latency per pixel); otherwise two pixels per warp.  Both give the
       // same tables (see cdf_fix).  Lane l of warp w copies the stream record
@@ -252,12 +319,21 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       }
       if (pr) pc[5] += 1;
       tick(1);
-      tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+      if constexpr (SHEAR) {
+        const long long c0 = pc != nullptr && threadIdx.x == 0 ? clock64() : 0;
+        tc_gather_shear_win(a.units, t.wrow, a.ring, d, t.tc, step, t.flag[3]);
+        __syncthreads();
+        if (pc != nullptr && threadIdx.x == 0) pc[13] += clock64() - c0;
+        tc_network<NT>(d, t.tc, t.flag[2], pc, true);
+      } else {
+        tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+      }
       if constexpr (SAMPLE) {
-        if (wide) sample_tile<32, NW>(a, t, n);
-        else sample_tile<kGW, NW>(a, t, n);
+        if (wide) sample_tile<32, NW, SHEAR>(a, t, n);
+        else sample_tile<kGW, NW, SHEAR>(a, t, n);
         __syncthreads();
         tick(3);
+        base += n;
         continue;
       }
       cp_async_wait_all();
@@ -271,10 +347,11 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       }
       __syncwarp();  // the warp's records are visible to all its lanes
       tick(2);
-      if (wide) code_tile<32, NW>(a, t, n, pc);
-      else code_tile<kGW, NW>(a, t, n, pc);
+      if (wide) code_tile<32, NW, SHEAR>(a, t, n, pc);
+      else code_tile<kGW, NW, SHEAR>(a, t, n, pc);
       __syncthreads();
       tick(3);
+      base += n;
     }
     if (step + 1 == a.T) break;
     const unsigned target = (unsigned)step + 1u;
@@ -285,7 +362,10 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       tick(0);
       lo = (long long)F * blockIdx.x / G;
       hi = (long long)F * (blockIdx.x + 1) / G;
-      if (lo < hi) fill_slots(step + 1, lo, (int)min((long long)MT, hi - lo), NS);
+      if (lo < hi) {
+        if constexpr (SHEAR) fill_slots_shear(step + 1, lo, (int)min((long long)MT, hi - lo), NS);
+        else fill_slots(step + 1, lo, (int)min((long long)MT, hi - lo), NS);
+      }
       tick(1);
     }
     if (G > 1) {
@@ -319,17 +399,20 @@ size_t decode_smem_bytes(const Dims& d, int n_units) {
   return tile_smem_bytes(d, n_units, decode_threads_of(d.prec) / kGW, true);
 }
 
-static const void* decode_fn(int prec, bool sample = false) {
+static const void* decode_fn(int prec, bool sample = false, bool win = false) {
+  if (win)
+    return sample ? (const void*)decode_kernel<PREC_BF16, true, true>
+                  : (const void*)decode_kernel<PREC_BF16, false, true>;
   if (sample)
-    return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16, true>
-                             : (const void*)decode_kernel<PREC_FP32, true>;
-  return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16, false>
-                           : (const void*)decode_kernel<PREC_FP32, false>;
+    return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16, true, false>
+                             : (const void*)decode_kernel<PREC_FP32, true, false>;
+  return prec == PREC_BF16 ? (const void*)decode_kernel<PREC_BF16, false, false>
+                           : (const void*)decode_kernel<PREC_FP32, false, false>;
 }
 
-int decode_max_grid(const DeviceModel& m, int n_units, int sm_count, bool sample) {
+int decode_max_grid(const DeviceModel& m, int n_units, int sm_count, bool sample, bool win) {
   const size_t smem = decode_smem_bytes(m.d, n_units);
-  const void* fn = decode_fn(m.d.prec, sample);
+  const void* fn = decode_fn(m.d.prec, sample, win);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -366,8 +449,10 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   a.prof = b.prof;
   a.times = b.times;
   a.n_times = b.n_times;
+  a.ring = b.ring;
+  const bool win = b.ring != nullptr && sched == SCHED_WAVEFRONT;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
-  const void* fn = decode_fn(m.d.prec);
+  const void* fn = decode_fn(m.d.prec, false, win);
   const int nt = decode_threads_of(m.d.prec);
   if (set_attr &&
       (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -399,8 +484,10 @@ cudaError_t launch_sample(const DeviceModel& m, const CodecBufs& b, int sched, i
   a.times = nullptr;
   a.n_times = 0;
   a.seed = seed;
+  a.ring = b.ring;
+  const bool win = b.ring != nullptr && sched == SCHED_WAVEFRONT;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
-  const void* fn = decode_fn(m.d.prec, true);
+  const void* fn = decode_fn(m.d.prec, true, win);
   const int nt = decode_threads_of(m.d.prec);
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)

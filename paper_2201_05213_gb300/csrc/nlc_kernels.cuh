@@ -55,6 +55,7 @@ struct CodecBufs {
   unsigned long long* st_pos;
   // decoder
   StreamRec* st;
+  uint8_t* ring = nullptr;       // sheared wavefront decoder: 96 bytes per unit row
   unsigned* bar;                 // 2 words: arrivals, generation
   int* status;
   unsigned long long* prof = nullptr;  // decoder phase cycle counters (16), optional
@@ -82,7 +83,9 @@ cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t
 cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_t* in,
                           const unsigned long long* d_offsets, int layout, int patch, int sched,
                           int T, int grid, cudaStream_t s, bool set_attr = true);
-int decode_max_grid(const DeviceModel& m, int n_units, int sm_count, bool sample = false);
+// win: the sheared model's wavefront decoder (window tiles from the ring).
+int decode_max_grid(const DeviceModel& m, int n_units, int sm_count, bool sample = false,
+                    bool win = false);
 // The decoder's schedule and tables driven by a counter-based generator
 // instead of streams: draws the batch's pixels from the model.
 cudaError_t launch_sample(const DeviceModel& m, const CodecBufs& b, int sched, int T, int grid,

@@ -38,8 +38,12 @@ constexpr unsigned kMbarSpin = 1u << 22;
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
+// Rows of the sheared decoder's window tile: a tile of 128 output rows reads
+// window rows m .. m + h (h <= 3), rounded up to a multiple of 8.
+constexpr int kWinRows = 136;
+
 struct TcPlan {
-  int w0, w1[kMaxR], w2[kMaxR], wh, bias, p, mbar, tslot, end;
+  int w0, w1[kMaxR], w2[kMaxR], wh, w0s, bias, p, mbar, tslot, end;
 };
 
 __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
@@ -55,11 +59,18 @@ __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
   }
   p.wh = o;
   o += d.NOp * d.C * 2;
+  // sheared first layer: h+1 tiles [C][Fsp], one per window row (top first)
+  p.w0s = o;
+  if (d.shear) o += (d.h + 1) * d.C * d.Fsp * 2;
   p.bias = o;
   o += (d.C + 2 * d.R * d.C + d.NOp) * 4;
   o = align_up(o, 128);
-  p.p = o;  // P[m][ldP] FP32, aliased with the BF16 context tile X
+  p.p = o;  // P[m][ldP] FP32, aliased with the BF16 context tile(s) X
   int pbytes = kTcM * d.ldP * 4, xbytes = kTcM * d.Fp * 2;
+  if (d.shear) {
+    const int per_px = (d.h + 1) * kTcM * d.Fsp * 2, win = d.Fsp * kWinRows * 2;
+    xbytes = per_px > win ? per_px : win;
+  }
   o += pbytes > xbytes ? pbytes : xbytes;
   o = align_up(o, 16);
   p.mbar = o;
@@ -71,8 +82,13 @@ __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
 }
 
 __host__ __device__ inline size_t tc_smem_bytes(const Dims& d) { return (size_t)tc_plan(d).end; }
-__host__ __device__ inline size_t umma_halves(const Dims& d) {
+// BF16 weight tiles: the tap-ordered first layer, the residual blocks and the
+// head (umma_plain_halves), then, for a sheared model, the sheared first layer.
+__host__ __device__ inline size_t umma_plain_halves(const Dims& d) {
   return (size_t)d.C * d.Fp + 2 * (size_t)d.R * d.C * d.C + (size_t)d.NOp * d.C;
+}
+__host__ __device__ inline size_t umma_halves(const Dims& d) {
+  return umma_plain_halves(d) + (d.shear ? (size_t)(d.h + 1) * d.C * d.Fsp : 0);
 }
 __host__ __device__ inline size_t bias_floats(const Dims& d) { return (size_t)d.C + 2 * (size_t)d.R * d.C + d.NOp; }
 
@@ -330,6 +346,171 @@ __device__ __noinline__ void tc_gather(const Unit* units, const PixSlot* slots, 
   }
 }
 
+// --- sheared first layer (Section 3.1, Fig. 5) ---------------------------------
+// Window row dd (0 = top, h = the pixel's own row) of pixel (i, j) at
+// wavefront step t = j + (h+1) i: unit row i - h + dd, the Ws = h(h+2)
+// sheared columns t - Ws .. t - 1, i.e. image columns j0 .. j0 + Ws - 1 with
+// j0 = j + (h+1)(h - dd) - Ws; feature 3q + c is channel c of window column
+// q (2v - 255, 0 outside the unit), features 3 Ws .. Fsp - 1 are 0.  The
+// sheared kernels give the taps of Eq. 3 their weights and every other
+// window position 0, so the layer equals the masked one.
+
+// Writes the Fsp features of one window row (3 Ws bytes at the realigned
+// words al[], zero outside columns [ca, cb) of the window) as BF16 8-feature
+// chunks: chunk kc to dst(kc).
+template <class Dst>
+__device__ __forceinline__ void shear_row_features(const uint32_t (&al)[12], int Ws, int Fsp,
+                                                   int ca, int cb, bool ok, Dst dst) {
+#pragma unroll
+  for (int kc = 0; kc < 6; kc++) {
+    if (kc >= Fsp / 8) break;
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      float xv[2];
+#pragma unroll
+      for (int f = 0; f < 2; f++) {
+        const int k = 8 * kc + e + f, q = k / 3;
+        const int v = (int)((al[(k >> 2) < 12 ? (k >> 2) : 11] >> (8 * (k & 3))) & 0xFFu);
+        xv[f] = (k < 3 * Ws && ok && q >= ca && q < cb) ? (float)(2 * v - 255) : 0.f;
+      }
+      pk[e / 2] = pack_bf16(xv[0], xv[1]);
+    }
+    *dst(kc) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+// Per-pixel window rows: h+1 tiles [128][Fsp] (canonical K-major), tile dd
+// at X + dd * 128 * Fsp.  One lane per (pixel m, window row dd), reading the
+// aligned 32-bit words that hold at least one byte of the row inside the
+// unit, as tc_gather does.
+template <bool kCoherent>
+__device__ __noinline__ void tc_gather_shear_px(const Unit* units, const PixSlot* slots,
+                                                const Dims& d, TcSmem& t, int n_valid) {
+  const int h = d.h, Ws = d.Ws, Fsp = d.Fsp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int dd = lane >> 3;
+  for (int mb = 8 * warp; mb < n_valid; mb += 8 * (int)(blockDim.x >> 5)) {
+    const int m = mb + (lane & 7);
+    if (dd > h || m >= n_valid) continue;
+    const PixSlot s = slots[m];
+    const Unit u = units[s.unit];
+    const int y = s.i - h + dd;
+    const int x0 = s.j + (h + 1) * (h - dd) - Ws;
+    const int ca = x0 < 0 ? -x0 : 0;
+    const int cb = min(Ws, u.Wu - x0);
+    const bool row_ok = y >= 0 && ca < cb;
+    uint32_t wv[13];
+#pragma unroll
+    for (int q = 0; q < 13; q++) wv[q] = 0u;
+    uint32_t sh = 0;
+    if (row_ok) {
+      const uintptr_t row = (uintptr_t)(u.img + ((long long)(u.y0 + y) * u.img_W + u.x0) * 3);
+      const uintptr_t lo = row + (uintptr_t)(3 * (long long)x0);
+      const uintptr_t a = lo + 3 * ca, b = lo + 3 * cb;
+      const uintptr_t w0 = lo & ~(uintptr_t)3;
+      sh = 8u * (uint32_t)(lo & 3);
+#pragma unroll
+      for (int q = 0; q < 13; q++) {
+        const uintptr_t wa = w0 + 4 * q;
+        if (wa + 4 > a && wa < b) {
+          const uint32_t* p = reinterpret_cast<const uint32_t*>(wa);
+          wv[q] = kCoherent ? ld_cg_u32(p) : *p;
+        }
+      }
+    }
+    uint32_t al[12];
+#pragma unroll
+    for (int q = 0; q < 12; q++) al[q] = __funnelshift_r(wv[q], wv[q + 1], sh);
+    uint16_t* X = t.X + (size_t)dd * kTcM * Fsp;
+    shear_row_features(al, Ws, Fsp, ca, cb, row_ok, [&](int kc) {
+      return reinterpret_cast<uint4*>(X + umma_off(m, 8 * kc, Fsp));
+    });
+  }
+}
+
+// Bytes of a unit row in the sheared ring: the pixel of sheared column c is
+// stored twice, at slots c mod 16 and c mod 16 + 16 (3 bytes each), so that
+// the Ws <= 15 columns before any column are one contiguous byte range.
+constexpr int kRingRowBytes = 96;
+
+// Window tile of a sheared wavefront step, K-chunk-major: feature k of window
+// row rho at X + (k/8) * kWinRows * 8 + rho * 8 + k % 8 (BF16), so that
+// consecutive rows are 16 bytes apart and the A operand of window row dd of
+// output row m is the tile started dd rows further.  wrow[rho] = (unit, unit
+// row) of window row rho (unit -1: a zero row); the decoded pixels come from
+// the units' sheared rings (unit u's row r at ring + 96 (u.ring_row + r)).
+static __device__ __noinline__ void tc_gather_shear_win(const Unit* units, const int2* wrow,
+                                                 const uint8_t* ring, const Dims& d, TcSmem& t,
+                                                 int step, int n_rows) {
+  const int h = d.h, Ws = d.Ws, Fsp = d.Fsp;
+  // window columns step - Ws .. step - 1: ring bytes from 3 ((step - Ws) mod 16)
+  const int c0 = step - Ws;
+  const int b0 = 3 * (c0 & 15);
+  for (int rho = threadIdx.x; rho < kWinRows; rho += blockDim.x) {
+    const int2 wr = rho < n_rows ? wrow[rho] : make_int2(-1, 0);
+    uint32_t wv[13];
+#pragma unroll
+    for (int q = 0; q < 13; q++) wv[q] = 0u;
+    int ca = 0, cb = 0;
+    if (wr.x >= 0 && wr.y >= 0) {
+      const Unit u = units[wr.x];
+      // columns q of the window inside the unit: image column c0 + q - (h+1) r
+      const int j0 = c0 - (h + 1) * wr.y;
+      ca = j0 < 0 ? -j0 : 0;
+      cb = min(Ws, u.Wu - j0);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(
+          ring + (long long)kRingRowBytes * (u.ring_row + wr.y) + (b0 & ~3));
+#pragma unroll
+      for (int q = 0; q < 13; q++)
+        if (4 * q < kRingRowBytes - (b0 & ~3)) wv[q] = ld_cg_u32(src + q);
+    }
+    uint32_t al[12];
+    const uint32_t sh = 8u * (uint32_t)(b0 & 3);
+#pragma unroll
+    for (int q = 0; q < 12; q++) al[q] = __funnelshift_r(wv[q], wv[q + 1], sh);
+    uint16_t* X = t.X;
+    shear_row_features(al, Ws, Fsp, ca, cb, ca < cb, [&](int kc) {
+      return reinterpret_cast<uint4*>(X + (size_t)kc * kWinRows * 8 + (size_t)rho * 8);
+    });
+  }
+}
+
+// The sheared first layer: for window rows dd = 0..h, Fsp/16 MMAs each of A =
+// window row dd of every output row against B = the sheared kernel tile dd,
+// accumulated in one chain (the same order for both A layouts, so the
+// per-pixel and the window tile give the same bits).
+__device__ __forceinline__ void tc_issue_shear(const TcSmem& t, const TcPlan& pl, const Dims& d,
+                                               bool win) {
+  if (threadIdx.x == 0) {
+    fence_after_sync();
+    const uint32_t idesc = idesc_bf16(kTcM, d.C);
+    const uint32_t bsbo = (uint32_t)(d.Fsp / 8) * 128u;
+    const int ks = d.Fsp / 16;
+    for (int dd = 0; dd <= d.h; dd++) {
+      uint32_t a_addr, a_lbo, a_sbo, a_step;
+      if (win) {  // rows 16 bytes apart, K chunks kWinRows rows apart
+        a_addr = smem_u32(t.X) + 16u * (uint32_t)dd;
+        a_lbo = (uint32_t)kWinRows * 16u;
+        a_sbo = 128u;
+        a_step = 2u * a_lbo;
+      } else {  // tile dd, canonical
+        a_addr = smem_u32(t.X + (size_t)dd * kTcM * d.Fsp);
+        a_lbo = 128u;
+        a_sbo = bsbo;
+        a_step = 256u;
+      }
+      const uint32_t b_addr = smem_u32(t.base + pl.w0s) + (uint32_t)(dd * d.C * d.Fsp * 2);
+      for (int k = 0; k < ks; k++) {
+        const uint64_t da = umma_desc(a_addr + (uint32_t)k * a_step, a_lbo, a_sbo);
+        const uint64_t db = umma_desc(b_addr + 256u * (uint32_t)k, 128u, bsbo);
+        mma_bf16(t.tmem, da, db, idesc, (dd > 0 || k > 0) ? 1u : 0u);
+      }
+    }
+    mma_commit(t.mbar);
+  }
+}
+
 // --- network -----------------------------------------------------------------
 __device__ __forceinline__ void tc_issue(const TcSmem& t, uint32_t a_off, uint32_t b_off, int Kd,
                                          int N) {
@@ -425,7 +606,8 @@ __device__ __forceinline__ void tmem_touch(uint32_t (&r)[8]) {
 // from MMA issue to completion to pc[14] and those of the epilogues (TMEM
 // loads, bias/ELU, operand stores, CTA barriers) to pc[15].
 template <int NT>
-__device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, long long* pc) {
+__device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, long long* pc,
+                                        bool win = false) {
   constexpr int NP = NT / 128;                // column parts
   constexpr int CH = (kMaxC / 8 + NP - 1) / NP;  // chunks of the hidden width per thread
   constexpr int HB = 4;                       // head chunks per load batch
@@ -483,7 +665,8 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
   fence_async_smem();
   __syncthreads();
   tick(15);
-  tc_issue(t, (uint32_t)pl.p, (uint32_t)pl.w0, d.Fp, C);
+  if (d.shear) tc_issue_shear(t, pl, d, win);
+  else tc_issue(t, (uint32_t)pl.p, (uint32_t)pl.w0, d.Fp, C);
   ok &= tc_wait(t);
   tick(14);
   hidden(t.bias, 0);

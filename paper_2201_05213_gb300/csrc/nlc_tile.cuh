@@ -211,6 +211,8 @@ struct TileSmem {
   int* pre;
   StreamRec* rec;  // decoder: the tile's stream records (kTileMax)
   uint32_t* win;   // decoder: per pixel, the 12 stream bytes from pos + 8, word-aligned
+  int* prow;       // sheared wavefront decoder: output row of the tile's pixel s
+  int2* wrow;      // sheared wavefront decoder: (unit, unit row) of window row rho
   long long* sh;
   long long* pc;  // 16 profiling accumulators (thread 0 only)
   int* flag;
@@ -235,7 +237,8 @@ __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int 
   }
   bytes = (bytes + 15) & ~(size_t)15;
   bytes += sizeof(WarpScratch) * groups;
-  if (dec) bytes += (sizeof(StreamRec) + 4 * sizeof(uint32_t)) * kTileMax;
+  if (dec) bytes += (sizeof(StreamRec) + 4 * sizeof(uint32_t) + sizeof(int)) * kTileMax +
+                    sizeof(int2) * kWinRows;
   bytes += sizeof(PixSlot) * kTileMax;
   bytes += sizeof(long long) * (33 + 16);
   bytes += sizeof(int) * (n_pre + 1 + 4);
@@ -265,11 +268,17 @@ __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, in
   off += sizeof(WarpScratch) * groups;
   t.rec = nullptr;
   t.win = nullptr;
+  t.prow = nullptr;
+  t.wrow = nullptr;
   if (dec) {
     t.rec = reinterpret_cast<StreamRec*>(smem + off);
     off += sizeof(StreamRec) * kTileMax;
     t.win = reinterpret_cast<uint32_t*>(smem + off);
     off += 4 * sizeof(uint32_t) * kTileMax;
+    t.wrow = reinterpret_cast<int2*>(smem + off);
+    off += sizeof(int2) * kWinRows;
+    t.prow = reinterpret_cast<int*>(smem + off);
+    off += sizeof(int) * kTileMax;
   }
   t.slots = reinterpret_cast<PixSlot*>(smem + off);
   off += sizeof(PixSlot) * kTileMax;
@@ -304,7 +313,8 @@ __device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* u
                                              int n_valid, long long* pc = nullptr) {
   if constexpr (PREC == PREC_BF16) {
     const long long c0 = pc != nullptr && threadIdx.x == 0 ? clock64() : 0;
-    tc_gather<kCoherent>(units, t.slots, m.d, t.tc, n_valid);
+    if (m.d.shear) tc_gather_shear_px<kCoherent>(units, t.slots, m.d, t.tc, n_valid);
+    else tc_gather<kCoherent>(units, t.slots, m.d, t.tc, n_valid);
     __syncthreads();
     if (pc != nullptr && threadIdx.x == 0) pc[13] += clock64() - c0;
     tc_network<NT>(m.d, t.tc, n_valid, pc);

@@ -64,7 +64,9 @@ struct TTPlan {
 __host__ __device__ inline int tile_bytes(int ncol) { return kTTM * ncol * 2; }
 
 __host__ __device__ inline TTPlan tt_plan(const Dims& d) {
-  const TcPlan tp = tc_plan(d);
+  Dims dp_ = d;
+  dp_.shear = 0;  // the trainer's tiles: the plain layout (no sheared first layer)
+  const TcPlan tp = tc_plan(dp_);
   TTPlan p;
   p.w0 = tp.w0;
   p.w1 = tp.w1[0];
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(kTT, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + pl.tslot);
   // weights (BF16 tiles) and biases
   {
-    const int nh = (int)umma_halves(d);
+    const int nh = (int)umma_plain_halves(d);  // a sheared model trains the same weights
     const uint4* src = reinterpret_cast<const uint4*>(umma);
     uint4* dst = reinterpret_cast<uint4*>(sm);
     for (int i = threadIdx.x; i < nh / 8; i += blockDim.x) dst[i] = src[i];

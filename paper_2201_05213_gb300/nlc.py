@@ -28,7 +28,7 @@ NLC_ERR_CUDA = 5
 NLC_ERR_TIMEOUT = 6
 NLC_ERR_UNSUPPORTED = 7
 
-NLC_FP32, NLC_BF16 = 0, 1
+NLC_FP32, NLC_BF16, NLC_BF16_SHEARED = 0, 1, 2
 NLC_SCHED_RASTER, NLC_SCHED_WAVEFRONT, NLC_SCHED_SEQUENTIAL = 0, 1, 2
 NLC_LAYOUT_UNIT, NLC_LAYOUT_ROW = 0, 1
 

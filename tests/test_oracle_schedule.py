@@ -142,3 +142,51 @@ def test_sheared_window_covers_context(h):
         dt = dx + o * dy
         assert -h * (h + 2) <= dt <= -1
     assert min(dx + o * dy for dy, dx in S.context_offsets(h)) == -h * (h + 2)
+
+
+@pytest.mark.parametrize("h", [1, 2, 3])
+def test_sheared_first_layer_equals_masked_layer(h):
+    # Section 3.1: on the sheared image (row i moved right by (h+1) i), the
+    # first layer is a plain correlation of Fig. 5's sheared kernels with the
+    # h+1 rows of the h(h+2) sheared columns before the pixel's own; in FP64
+    # it equals the masked layer on the context of Eq. 3 (zero padding).
+    rng = np.random.default_rng(h)
+    C, H, W = 3, 7, 9
+    ntap = 2 * h * (h + 1)
+    W0 = rng.normal(0, 1, (C, 3 * ntap))
+    img = rng.integers(0, 256, (H, W, 3))
+    x = (2.0 * img - 255.0) / 255.0
+    o = h + 1
+    Sx = S.shear(x, o)
+    Ws = h * (h + 2)
+    offs = S.context_offsets(h)
+    for oc in range(C):
+        # per input channel: the unmasked kernel rows, top first
+        kern = []
+        for c in range(3):
+            rows, p = [], 0
+            for dy in range(-h, 1):
+                n = 2 * h + 1 if dy < 0 else h
+                rows.append([W0[oc, 3 * (p + k) + c] for k in range(n)])
+                p += n
+            kern.append(np.array(S.sheared_kernel(rows, h), dtype=np.float64))
+        for i in range(H):
+            for j in range(W):
+                ref = 0.0
+                for p, (dy, dx) in enumerate(offs):
+                    ii, jj = i + dy, j + dx
+                    if 0 <= ii < H and 0 <= jj < W:
+                        ref += float(np.dot(W0[oc, 3 * p:3 * p + 3], x[ii, jj]))
+                t = j + o * i
+                got = 0.0
+                for dd in range(h + 1):
+                    r = i - h + dd
+                    if r < 0:
+                        continue
+                    for q in range(Ws):
+                        col = t - Ws + q
+                        if col < 0:
+                            continue
+                        for c in range(3):
+                            got += kern[c][dd][q] * Sx[r, col, c]
+                assert abs(got - ref) < 1e-12, (oc, i, j)
