@@ -91,7 +91,7 @@ static Dims make_dims(const nlc_model_cfg* c) {
   d.shear = c->precision == NLC_BF16_SHEARED ? 1 : 0;
   d.prec = d.shear ? NLC_BF16 : c->precision;
   d.Ws = c->h * (c->h + 2);
-  d.Fsp = (3 * d.Ws + 15) / 16 * 16;
+  d.Fsp = shear_row_features_n(c->h);  // 16, 32, 56 for h = 1, 2, 3
   return d;
 }
 
@@ -547,6 +547,8 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
     return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
   CodecBufs cb;
   const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
+  if (ring && b.ring_rows >= (1LL << 31) / kRingRowBytes)
+    return fail(NLC_ERR_UNSUPPORTED, "batch too large for the sheared decoder's rings");
   size_t need = layout_bufs(b, nullptr, cb, x->d_status, false, ring);
   if ((rc = ensure_ws(x, need))) return rc;
   layout_bufs(b, x->ws, cb, x->d_status, false, ring);
@@ -595,6 +597,8 @@ extern "C" int nlc_sample(nlc_ctx* x, const nlc_image_out* outs, int n, int patc
     return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
   CodecBufs cb;
   const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
+  if (ring && b.ring_rows >= (1LL << 31) / kRingRowBytes)
+    return fail(NLC_ERR_UNSUPPORTED, "batch too large for the sheared decoder's rings");
   size_t need = layout_bufs(b, nullptr, cb, x->d_status, false, ring);
   if ((rc = ensure_ws(x, need))) return rc;
   layout_bufs(b, x->ws, cb, x->d_status, false, ring);
@@ -859,6 +863,9 @@ extern "C" int nlc_plan_decode(nlc_ctx* x, const nlc_image_out* outs, int n, int
   if (rc) return rc;
   if (decode_smem_bytes(x->d, (int)b.units.size()) > 227 * 1024)
     return fail(NLC_ERR_UNSUPPORTED, "too many coding units in one call (%zu)", b.units.size());
+  const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
+  if (ring && b.ring_rows >= (1LL << 31) / kRingRowBytes)
+    return fail(NLC_ERR_UNSUPPORTED, "batch too large for the sheared decoder's rings");
   nlc_plan* p = new nlc_plan();
   p->x = x;
   p->n = n;
@@ -869,7 +876,6 @@ extern "C" int nlc_plan_decode(nlc_ctx* x, const nlc_image_out* outs, int n, int
   p->max_front = b.max_front;
   p->n_units = (int)b.units.size();
   p->px_per_cta = x->px_per_cta;
-  const bool ring = x->d.shear && schedule == NLC_SCHED_WAVEFRONT;
   const size_t need = layout_bufs(b, nullptr, p->cb, x->d_status, false, ring);
   cudaError_t e = cudaMalloc((void**)&p->d_buf, std::max<size_t>(need, 256));
   if (e != cudaSuccess) {

@@ -99,11 +99,15 @@ __global__ void repack_umma_kernel(Dims d, const float* __restrict__ w, uint16_t
     int kind;         // 0 W0, 1 hidden, 2 head, 3 sheared W0
     int dd = 0;       // sheared: window row (0 = top, h = the pixel's own row)
     const long long plain = (long long)umma_plain_halves(d);
+    int c_lo = 0;  // sheared: first 8-feature chunk of window row dd's MMAs
     if (o >= plain) {
       o -= plain;
-      dd = (int)(o / ((long long)C * d.Fsp));
-      o %= (long long)C * d.Fsp;
-      Kd = d.Fsp; wbase = 0; kind = 3;
+      int ks = 0;
+      dd = 0;
+      while (dd < d.h && o >= (long long)shear_tile_off(d, dd + 1)) dd++;
+      o -= shear_tile_off(d, dd);
+      shear_krange(d.h, d.Ws, dd, c_lo, ks);
+      Kd = 16 * ks; wbase = 0; kind = 3;
     } else if (o < (long long)C * Fp) {
       Kd = Fp; wbase = 0; kind = 0;
     } else {
@@ -125,10 +129,12 @@ __global__ void repack_umma_kernel(Dims d, const float* __restrict__ w, uint16_t
     }
     const int core = (int)(o / 64), within = (int)(o % 64);
     const int rb = core / (Kd / 8), kb = core % (Kd / 8);
-    const int r = rb * 8 + within / 8, k = kb * 8 + within % 8;
+    const int r = rb * 8 + within / 8;
+    int k = kb * 8 + within % 8;
     float v;
     if (kind == 0) v = k < F ? __fdiv_rn(w[(long long)r * F + k], 255.f) : 0.f;
     else if (kind == 3) {
+      k += 8 * c_lo;  // feature of the window row
       // window row dd, window column q = k / 3 (channel k % 3): the pixel at
       // row offset dy = dd - h and column offset dx = q - Ws + (h+1)(h - dd)
       // (the sheared column t - Ws + q of row i + dy, t = j + (h+1) i); its

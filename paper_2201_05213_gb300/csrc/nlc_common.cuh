@@ -42,14 +42,48 @@ enum Schedule { SCHED_RASTER = 0, SCHED_WAVEFRONT = 1 };
 // outputs in shared memory; odd, against bank conflicts).
 // shear = 1: the first layer is evaluated as the sheared kernels of Section
 // 3.1 (Fig. 5) over the h+1 rows of the h(h+2) sheared columns before the
-// pixel's own (Ws = h(h+2) pixels, Fsp = 3 Ws rounded up to 16 features per
-// window row); the network runs in BF16 (prec = PREC_BF16).
+// pixel's own (Ws = h(h+2) pixels, 3 Ws features per window row, stored in
+// rows of Fsp features, zero past 3 Ws); the network runs in BF16 (prec =
+// PREC_BF16).
 struct Dims {
   int h, C, R, K;
   int F, Fp, NO, NOp, ldP;
   int prec;
   int shear, Ws, Fsp;
 };
+
+// Sheared first layer, window row dd (0 = top): its taps sit at window
+// columns qa .. qa + n - 1 (n = 2h+1 above the pixel's row, h in it), qa =
+// Ws - (h+1)(h-dd) - h, i.e. features [3 qa, 3 (qa + n)); its MMAs cover
+// the features [8 c_lo, 8 c_lo + 16 ks) (whole 8-feature chunks, K = 16 per
+// MMA), the rest of the window row holds only zero weights.
+__host__ __device__ __forceinline__ void shear_krange(int h, int Ws, int dd, int& c_lo, int& ks) {
+  const int qa = Ws - (h + 1) * (h - dd) - h, n = dd < h ? 2 * h + 1 : h;
+  c_lo = (3 * qa) / 8;
+  ks = (3 * (qa + n) - 8 * c_lo + 15) / 16;
+}
+// Features per stored window row: every MMA's range inside it.
+__host__ __device__ __forceinline__ int shear_row_features_n(int h) {
+  const int Ws = h * (h + 2);
+  int f = 0;
+  for (int dd = 0; dd <= h; dd++) {
+    int c, k;
+    shear_krange(h, Ws, dd, c, k);
+    f = f > 8 * c + 16 * k ? f : 8 * c + 16 * k;
+  }
+  return f;
+}
+// Offset (BF16 elements) of window row dd's kernel tile [C][16 ks] among the
+// sheared tiles, and their total (dd = h + 1).
+__host__ __device__ __forceinline__ int shear_tile_off(const Dims& d, int dd) {
+  int off = 0;
+  for (int e = 0; e < dd; e++) {
+    int c, k;
+    shear_krange(d.h, d.Ws, e, c, k);
+    off += d.C * 16 * k;
+  }
+  return off;
+}
 
 // Precision byte of a container (and of the model's hash): 0 FP32, 1 BF16,
 // 2 BF16 with the sheared first layer.

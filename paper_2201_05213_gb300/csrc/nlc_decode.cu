@@ -45,12 +45,11 @@ __device__ __forceinline__ int group_slot(int warp, int l) {
 // pixels' stream records are in t.rec (visible to the warp), their windows
 // are being copied to t.win by the warp's lanes.  With pc non-null, thread 0
 // accumulates its sub-stage cycles in pc[8..12].
-// Stores a decoded pixel of sheared column tau = j + (h+1) i in its unit's
-// ring row (twice, at slots tau mod 16 and tau mod 16 + 16).
-__device__ __forceinline__ void ring_put(const DecodeArgs& a, const Unit& U, int i, int j,
-                                         const int (&v)[3]) {
-  const int tau = j + (a.m.d.h + 1) * i;
-  uint8_t* r = a.ring + (long long)kRingRowBytes * (U.ring_row + i) + 3 * (tau & 15);
+// Stores a decoded pixel in its unit's ring row at the byte offset rofs
+// that the tile's schedule computed (slots tau mod 16 and tau mod 16 + 16 of
+// its sheared column tau).
+__device__ __forceinline__ void ring_put(const DecodeArgs& a, int rofs, const int (&v)[3]) {
+  uint8_t* r = a.ring + rofs;
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     r[c] = (uint8_t)v[c];
@@ -123,7 +122,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       px[0] = (uint8_t)v[0];
       px[1] = (uint8_t)v[1];
       px[2] = (uint8_t)v[2];
-      if (SHEAR) ring_put(a, U, ps.i, ps.j, v);
+      if (SHEAR) ring_put(a, t.rofs[s], v);
       const int sid = ps.aux;
       const unsigned long long np = dec.pos + (unsigned long long)dec.used;
       uint32_t n0, n1;
@@ -173,7 +172,7 @@ __device__ __noinline__ void sample_tile(const DecodeArgs& a, const TileSmem& t,
       px[0] = (uint8_t)v[0];
       px[1] = (uint8_t)v[1];
       px[2] = (uint8_t)v[2];
-      if (SHEAR) ring_put(a, U, ps.i, ps.j, v);
+      if (SHEAR) ring_put(a, t.rofs[s], v);
     }
   }
 }
@@ -233,6 +232,8 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
         ps.i = fr.i_lo + (q - t.pre[lo2]);
         ps.j = front_col(U, step, ps.i, h, a.sched);
         ps.aux = U.stream_base + (a.layout == 1 ? ps.i : 0);
+        if constexpr (SHEAR)  // ring bytes of the pixel's sheared column j + (h+1) i
+          t.rofs[s] = kRingRowBytes * (U.ring_row + ps.i) + 3 * ((ps.j + (h + 1) * ps.i) & 15);
       }
       t.slots[s] = ps;
     }
@@ -244,12 +245,12 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   // output rows and window rows (the output rows stay below MT).
   auto fill_slots_shear = [&](int step, long long base, int nmax, int nt) {
     fill_slots(step, base, nmax, nt);
-    for (int r = threadIdx.x; r < kWinRows; r += nt) t.wrow[r] = make_int2(-1, 0);
     part_sync(nt);
     if (threadIdx.x < MT) {  // warps 0 .. MT/32 - 1
       const int s = threadIdx.x, w = s >> 5, l = s & 31;
       const bool valid = s < nmax;
-      const bool start = valid && (s == 0 || t.slots[s].unit != t.slots[s - 1].unit);
+      const int u = t.slots[s].unit;
+      const bool start = valid && (s == 0 || u != t.slots[s - 1].unit);
       const unsigned bal = __ballot_sync(0xffffffffu, start);
       if (l == 0) t.sh[w] = __popc(bal);
       asm volatile("bar.sync 2, %0;" ::"n"(MT) : "memory");
@@ -258,11 +259,9 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       const int seg = before + __popc(bal & (0xffffffffu >> (31 - l))) - 1;
       const int pr = s + h * seg;
       const bool fits = valid && pr < MT;
-      const unsigned fb = __ballot_sync(0xffffffffu, fits);
-      asm volatile("bar.sync 2, %0;" ::"n"(MT) : "memory");
-      if (l == 0) t.sh[w] = __popc(fb);
-      asm volatile("bar.sync 2, %0;" ::"n"(MT) : "memory");
-      const int n = (int)(t.sh[0] + t.sh[1] + t.sh[2] + t.sh[3]);
+      // the tile's last pixel: the next one is missing or would not fit
+      const bool valid1 = s + 1 < nmax;
+      const int pr1 = s + 1 + h * (seg + ((valid1 && t.slots[s + 1].unit != u) ? 1 : 0));
       t.prow[s] = pr;
       if (fits) {
         const PixSlot ps = t.slots[s];
@@ -270,11 +269,11 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
         if (start)
           for (int k = 1; k <= h; k++)
             t.wrow[pr + h - k] = make_int2(ps.i - k >= 0 ? ps.unit : -1, ps.i - k);
-      }
-      if (s == n - 1) {
-        t.flag[1] = n;
-        t.flag[2] = pr + 1;
-        t.flag[3] = pr + 1 + h;
+        if (!valid1 || pr1 >= MT) {
+          t.flag[1] = s + 1;
+          t.flag[2] = pr + 1;
+          t.flag[3] = pr + 1 + h;
+        }
       }
     }
   };

@@ -43,8 +43,12 @@ __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a *
 constexpr int kWinRows = 136;
 
 struct TcPlan {
-  int w0, w1[kMaxR], w2[kMaxR], wh, w0s, bias, p, mbar, tslot, end;
+  int w0, w1[kMaxR], w2[kMaxR], wh, w0s, bias, p, mbar, tslot, sdesc, end;
 };
+
+// Sheared first layer: at most 8 MMAs (7 for h = 3); their (A, B)
+// descriptors for both A layouts, built once per CTA, behind a count.
+constexpr int kShearMaxMma = 8;
 
 __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
   TcPlan p;
@@ -59,9 +63,10 @@ __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
   }
   p.wh = o;
   o += d.NOp * d.C * 2;
-  // sheared first layer: h+1 tiles [C][Fsp], one per window row (top first)
+  // sheared first layer: h+1 tiles [C][16 ks(dd)], one per window row (top
+  // first), each only over the window row's tap range
   p.w0s = o;
-  if (d.shear) o += (d.h + 1) * d.C * d.Fsp * 2;
+  if (d.shear) o += shear_tile_off(d, d.h + 1) * 2;
   p.bias = o;
   o += (d.C + 2 * d.R * d.C + d.NOp) * 4;
   o = align_up(o, 128);
@@ -77,6 +82,9 @@ __host__ __device__ inline TcPlan tc_plan(const Dims& d) {
   o += 8;
   p.tslot = o;
   o += 8;
+  p.sdesc = o;  // [0]: count (set by tc_setup for every model); then (a_px, a_win, b) per MMA
+  o += 8;
+  if (d.shear) o += 3 * 8 * kShearMaxMma;
   p.end = align_up(o, 128);
   return p;
 }
@@ -88,7 +96,7 @@ __host__ __device__ inline size_t umma_plain_halves(const Dims& d) {
   return (size_t)d.C * d.Fp + 2 * (size_t)d.R * d.C * d.C + (size_t)d.NOp * d.C;
 }
 __host__ __device__ inline size_t umma_halves(const Dims& d) {
-  return umma_plain_halves(d) + (d.shear ? (size_t)(d.h + 1) * d.C * d.Fsp : 0);
+  return umma_plain_halves(d) + (d.shear ? (size_t)shear_tile_off(d, d.h + 1) : 0);
 }
 __host__ __device__ inline size_t bias_floats(const Dims& d) { return (size_t)d.C + 2 * (size_t)d.R * d.C + d.NOp; }
 
@@ -99,6 +107,7 @@ struct TcSmem {
   float* bias;
   uint64_t* mbar;
   uint32_t* tslot;
+  uint64_t* sdesc;  // sheared first layer's descriptors (thread 0 only)
   uint32_t tmem;
   uint32_t phase;
   int ok;
@@ -121,6 +130,7 @@ __device__ __forceinline__ TcSmem tc_carve(const Dims& d, unsigned char* smem) {
   t.bias = reinterpret_cast<float*>(smem + p.bias);
   t.mbar = reinterpret_cast<uint64_t*>(smem + p.mbar);
   t.tslot = reinterpret_cast<uint32_t*>(smem + p.tslot);
+  t.sdesc = reinterpret_cast<uint64_t*>(smem + p.sdesc);
   t.tmem = 0;
   t.phase = 0;
   t.ok = 1;
@@ -242,6 +252,7 @@ __device__ __forceinline__ void tc_setup(TcSmem& t) {
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(t.mbar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    t.sdesc[0] = 0;  // the sheared layer's descriptors are built on first use
   }
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -362,7 +373,7 @@ template <class Dst>
 __device__ __forceinline__ void shear_row_features(const uint32_t (&al)[12], int Ws, int Fsp,
                                                    int ca, int cb, bool ok, Dst dst) {
 #pragma unroll
-  for (int kc = 0; kc < 6; kc++) {
+  for (int kc = 0; kc < 7; kc++) {  // Fsp <= 56
     if (kc >= Fsp / 8) break;
     uint32_t pk[4];
 #pragma unroll
@@ -441,72 +452,88 @@ constexpr int kRingRowBytes = 96;
 // row) of window row rho (unit -1: a zero row); the decoded pixels come from
 // the units' sheared rings (unit u's row r at ring + 96 (u.ring_row + r)).
 static __device__ __noinline__ void tc_gather_shear_win(const Unit* units, const int2* wrow,
-                                                 const uint8_t* ring, const Dims& d, TcSmem& t,
-                                                 int step, int n_rows) {
-  const int h = d.h, Ws = d.Ws, Fsp = d.Fsp;
-  // window columns step - Ws .. step - 1: ring bytes from 3 ((step - Ws) mod 16)
+                                                        const uint8_t* ring, const Dims& d,
+                                                        TcSmem& t, int step, int n_rows) {
+  const int h = d.h, Ws = d.Ws, nch = d.Fsp / 8;
+  // window columns step - Ws .. step - 1: ring bytes from 3 ((step - Ws) mod 16);
+  // feature k of a window row is byte k of that range
   const int c0 = step - Ws;
   const int b0 = 3 * (c0 & 15);
-  for (int rho = threadIdx.x; rho < kWinRows; rho += blockDim.x) {
-    const int2 wr = rho < n_rows ? wrow[rho] : make_int2(-1, 0);
-    uint32_t wv[13];
-#pragma unroll
-    for (int q = 0; q < 13; q++) wv[q] = 0u;
+  uint16_t* X = t.X;
+  // one item per (window row, 8-feature chunk); rows past n_rows feed only
+  // output rows that hold no pixel and are left as they are
+  for (int it = threadIdx.x; it < n_rows * nch; it += blockDim.x) {
+    const int rho = it / nch, kc = it - rho * nch;
+    const int2 wr = wrow[rho];
+    uint32_t w0 = 0u, w1 = 0u, w2 = 0u;
     int ca = 0, cb = 0;
-    if (wr.x >= 0 && wr.y >= 0) {
+    const int bs = b0 + 8 * kc;  // first ring byte of the chunk (<= 85)
+    if (wr.x >= 0 && wr.y >= 0 && 8 * kc < 3 * Ws) {
       const Unit u = units[wr.x];
-      // columns q of the window inside the unit: image column c0 + q - (h+1) r
-      const int j0 = c0 - (h + 1) * wr.y;
+      const int j0 = c0 - (h + 1) * wr.y;  // image column of window column 0
       ca = j0 < 0 ? -j0 : 0;
       cb = min(Ws, u.Wu - j0);
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(
-          ring + (long long)kRingRowBytes * (u.ring_row + wr.y) + (b0 & ~3));
-#pragma unroll
-      for (int q = 0; q < 13; q++)
-        if (4 * q < kRingRowBytes - (b0 & ~3)) wv[q] = ld_cg_u32(src + q);
+      if (ca < cb) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(
+            ring + (long long)kRingRowBytes * (u.ring_row + wr.y) + (bs & ~3));
+        w0 = ld_cg_u32(src);
+        w1 = ld_cg_u32(src + 1);
+        if ((bs & ~3) + 8 < kRingRowBytes) w2 = ld_cg_u32(src + 2);
+      }
     }
-    uint32_t al[12];
-    const uint32_t sh = 8u * (uint32_t)(b0 & 3);
+    const uint32_t sh = 8u * (uint32_t)(bs & 3);
+    const uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+    uint32_t pk[4];
 #pragma unroll
-    for (int q = 0; q < 12; q++) al[q] = __funnelshift_r(wv[q], wv[q + 1], sh);
-    uint16_t* X = t.X;
-    shear_row_features(al, Ws, Fsp, ca, cb, ca < cb, [&](int kc) {
-      return reinterpret_cast<uint4*>(X + (size_t)kc * kWinRows * 8 + (size_t)rho * 8);
-    });
+    for (int e = 0; e < 8; e += 2) {
+      float xv[2];
+#pragma unroll
+      for (int f = 0; f < 2; f++) {
+        const int k = 8 * kc + e + f, q = k / 3;
+        const uint32_t byte = ((e + f) < 4 ? lo >> (8 * (e + f)) : hi >> (8 * (e + f - 4))) & 0xFFu;
+        xv[f] = (k < 3 * Ws && q >= ca && q < cb) ? (float)(2 * (int)byte - 255) : 0.f;
+      }
+      pk[e / 2] = pack_bf16(xv[0], xv[1]);
+    }
+    *reinterpret_cast<uint4*>(X + (size_t)kc * kWinRows * 8 + (size_t)rho * 8) =
+        make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
-// The sheared first layer: for window rows dd = 0..h, Fsp/16 MMAs each of A =
-// window row dd of every output row against B = the sheared kernel tile dd,
-// accumulated in one chain (the same order for both A layouts, so the
-// per-pixel and the window tile give the same bits).
+// The sheared first layer: for window rows dd = 0..h, ks(dd) MMAs of A = the
+// tap range of window row dd of every output row against B = its sheared
+// kernel tile, accumulated in one chain (the same instructions for both A
+// layouts, so the per-pixel and the window tile give the same bits).
 __device__ __forceinline__ void tc_issue_shear(const TcSmem& t, const TcPlan& pl, const Dims& d,
                                                bool win) {
   if (threadIdx.x == 0) {
     fence_after_sync();
-    const uint32_t idesc = idesc_bf16(kTcM, d.C);
-    const uint32_t bsbo = (uint32_t)(d.Fsp / 8) * 128u;
-    const int ks = d.Fsp / 16;
-    for (int dd = 0; dd <= d.h; dd++) {
-      uint32_t a_addr, a_lbo, a_sbo, a_step;
-      if (win) {  // rows 16 bytes apart, K chunks kWinRows rows apart
-        a_addr = smem_u32(t.X) + 16u * (uint32_t)dd;
-        a_lbo = (uint32_t)kWinRows * 16u;
-        a_sbo = 128u;
-        a_step = 2u * a_lbo;
-      } else {  // tile dd, canonical
-        a_addr = smem_u32(t.X + (size_t)dd * kTcM * d.Fsp);
-        a_lbo = 128u;
-        a_sbo = bsbo;
-        a_step = 256u;
+    uint64_t* sd = t.sdesc;
+    if (sd[0] == 0) {  // first use by this CTA: every MMA's descriptors
+      int n = 0;
+      for (int dd = 0; dd <= d.h; dd++) {
+        int c_lo, ks;
+        shear_krange(d.h, d.Ws, dd, c_lo, ks);
+        // window tile: rows 16 bytes apart, K chunks kWinRows rows apart
+        const uint32_t w_lbo = (uint32_t)kWinRows * 16u;
+        const uint32_t aw = smem_u32(t.X) + 16u * (uint32_t)dd + (uint32_t)c_lo * w_lbo;
+        // per-pixel tile dd, canonical
+        const uint32_t ap = smem_u32(t.X + (size_t)dd * kTcM * d.Fsp) + 128u * (uint32_t)c_lo;
+        const uint32_t p_sbo = (uint32_t)(d.Fsp / 8) * 128u;
+        const uint32_t b = smem_u32(t.base + pl.w0s) + (uint32_t)(shear_tile_off(d, dd) * 2);
+        const uint32_t b_sbo = (uint32_t)(2 * ks) * 128u;
+        for (int k = 0; k < ks; k++, n++) {
+          sd[1 + 3 * n] = umma_desc(ap + 256u * (uint32_t)k, 128u, p_sbo);
+          sd[2 + 3 * n] = umma_desc(aw + 2u * w_lbo * (uint32_t)k, w_lbo, 128u);
+          sd[3 + 3 * n] = umma_desc(b + 256u * (uint32_t)k, 128u, b_sbo);
+        }
       }
-      const uint32_t b_addr = smem_u32(t.base + pl.w0s) + (uint32_t)(dd * d.C * d.Fsp * 2);
-      for (int k = 0; k < ks; k++) {
-        const uint64_t da = umma_desc(a_addr + (uint32_t)k * a_step, a_lbo, a_sbo);
-        const uint64_t db = umma_desc(b_addr + 256u * (uint32_t)k, 128u, bsbo);
-        mma_bf16(t.tmem, da, db, idesc, (dd > 0 || k > 0) ? 1u : 0u);
-      }
+      sd[0] = (uint64_t)n;
     }
+    const uint32_t idesc = idesc_bf16(kTcM, d.C);
+    const int n = (int)sd[0];
+    for (int k = 0; k < n; k++)
+      mma_bf16(t.tmem, sd[(win ? 2 : 1) + 3 * k], sd[3 + 3 * k], idesc, k > 0 ? 1u : 0u);
     mma_commit(t.mbar);
   }
 }

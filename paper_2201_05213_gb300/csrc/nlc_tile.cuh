@@ -212,6 +212,7 @@ struct TileSmem {
   StreamRec* rec;  // decoder: the tile's stream records (kTileMax)
   uint32_t* win;   // decoder: per pixel, the 12 stream bytes from pos + 8, word-aligned
   int* prow;       // sheared wavefront decoder: output row of the tile's pixel s
+  int* rofs;       // sheared wavefront decoder: ring byte offset of the tile's pixel s
   int2* wrow;      // sheared wavefront decoder: (unit, unit row) of window row rho
   long long* sh;
   long long* pc;  // 16 profiling accumulators (thread 0 only)
@@ -237,7 +238,7 @@ __host__ __device__ inline size_t tile_smem_bytes(const Dims& d, int n_pre, int 
   }
   bytes = (bytes + 15) & ~(size_t)15;
   bytes += sizeof(WarpScratch) * groups;
-  if (dec) bytes += (sizeof(StreamRec) + 4 * sizeof(uint32_t) + sizeof(int)) * kTileMax +
+  if (dec) bytes += (sizeof(StreamRec) + 4 * sizeof(uint32_t) + 2 * sizeof(int)) * kTileMax +
                     sizeof(int2) * kWinRows;
   bytes += sizeof(PixSlot) * kTileMax;
   bytes += sizeof(long long) * (33 + 16);
@@ -269,6 +270,7 @@ __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, in
   t.rec = nullptr;
   t.win = nullptr;
   t.prow = nullptr;
+  t.rofs = nullptr;
   t.wrow = nullptr;
   if (dec) {
     t.rec = reinterpret_cast<StreamRec*>(smem + off);
@@ -278,6 +280,8 @@ __device__ __forceinline__ TileSmem carve(const Dims& d, unsigned char* smem, in
     t.wrow = reinterpret_cast<int2*>(smem + off);
     off += sizeof(int2) * kWinRows;
     t.prow = reinterpret_cast<int*>(smem + off);
+    off += sizeof(int) * kTileMax;
+    t.rofs = reinterpret_cast<int*>(smem + off);
     off += sizeof(int) * kTileMax;
   }
   t.slots = reinterpret_cast<PixSlot*>(smem + off);
