@@ -147,6 +147,16 @@ int nlc_sync_status(nlc_ctx* ctx, nlc_stream stream);
  * be co-resident). */
 int nlc_set_tuning(nlc_ctx* ctx, int px_per_cta, int max_ctas);
 
+/* Limits of the decoder's bounded waits (also the sampler's): polls of the
+ * grid barrier between wavefront steps and of an MMA's completion before the
+ * wait gives up (0 = the defaults, 2^25 and 2^22 polls, far beyond any
+ * normal wait).  A wait that gives up records NLC_ERR_TIMEOUT in the
+ * context's status and releases every CTA of the launch, which leaves the
+ * decode loop (an MMA wait first waits, bounded, for the MMAs it issued);
+ * the context stays usable.  Small limits exist to exercise that path: a
+ * reduced MMA limit counts non-blocking tests of the completion. */
+int nlc_set_wait_limits(nlc_ctx* ctx, uint32_t grid_polls, uint32_t mma_polls);
+
 /* Decoder phase profile (per-step latency against the dependency-bound step
  * count of Section 3).  enable != 0 makes the following nlc_decompress calls
  * and nlc_plan_run calls (a captured graph keeps the setting of its capture)

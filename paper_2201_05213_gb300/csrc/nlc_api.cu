@@ -62,6 +62,7 @@ struct nlc_ctx {
   bool prof_on = false;                  // launches receive d_prof only while profiling
   unsigned long long* d_times = nullptr;  // caller's buffer of decoder step end times
   long long n_times = 0;
+  unsigned spin_limit = 0, mma_limit = 0;  // decoder wait limits (0: defaults)
 };
 
 static unsigned long long* prof_ptr(const nlc_ctx* x) { return x->prof_on ? x->d_prof : nullptr; }
@@ -298,6 +299,13 @@ extern "C" int nlc_decode_profile(nlc_ctx* x, int enable, uint64_t* h_counters) 
   if (h_counters || enable != (int)x->prof_on)
     CUDA_TRY(cudaMemset(x->d_prof, 0, 16 * sizeof(uint64_t)));
   x->prof_on = enable != 0;
+  return NLC_OK;
+}
+
+extern "C" int nlc_set_wait_limits(nlc_ctx* x, uint32_t grid_polls, uint32_t mma_polls) {
+  if (!x) return fail(NLC_ERR_ARG, "ctx is NULL");
+  x->spin_limit = grid_polls;
+  x->mma_limit = mma_polls;
   return NLC_OK;
 }
 
@@ -565,6 +573,8 @@ extern "C" int nlc_decompress(nlc_ctx* x, const uint8_t* d_in, const uint64_t* d
   cb.prof = prof_ptr(x);
   cb.times = x->d_times;
   cb.n_times = x->n_times;
+  cb.spin_limit = x->spin_limit;
+  cb.mma_limit = x->mma_limit;
   CUDA_TRY(launch_decode(m, cb, d_in, reinterpret_cast<const unsigned long long*>(d_offsets),
                          layout, patch, sched, (int)b.T, grid, s));
   return NLC_OK;
@@ -611,6 +621,8 @@ extern "C" int nlc_sample(nlc_ctx* x, const nlc_image_out* outs, int n, int patc
   int grid = (int)std::max(1LL, std::min<long long>(g, gmax));
   if ((long long)grid * b.T >= (1LL << 31) - 1) grid = 1;
   const int sched = schedule == NLC_SCHED_WAVEFRONT ? SCHED_WAVEFRONT : SCHED_RASTER;
+  cb.spin_limit = x->spin_limit;
+  cb.mma_limit = x->mma_limit;
   CUDA_TRY(launch_sample(m, cb, sched, (int)b.T, grid, (unsigned long long)seed, s));
   return NLC_OK;
 }
@@ -917,6 +929,8 @@ extern "C" int nlc_plan_run(nlc_plan* p, const uint8_t* d_in, const uint64_t* d_
   p->cb.prof = prof_ptr(p->x);  // as of this call (a captured graph keeps it)
   p->cb.times = p->x->d_times;
   p->cb.n_times = p->x->n_times;
+  p->cb.spin_limit = p->x->spin_limit;
+  p->cb.mma_limit = p->x->mma_limit;
   CUDA_TRY(launch_decode(model_view(p->x), p->cb, d_in,
                          reinterpret_cast<const unsigned long long*>(d_offsets), p->layout,
                          p->patch, p->sched, (int)p->T, p->grid, s, false));

@@ -216,7 +216,7 @@ __device__ __forceinline__ void grid_arrive(unsigned* count) {
 // synchronises.  Returns false if the decode must stop (a timeout here or
 // elsewhere).
 __device__ __forceinline__ bool grid_wait(unsigned* count, unsigned nblocks, unsigned target,
-                                          int* status, int* s_flag) {
+                                          int* status, int* s_flag, unsigned limit = kSpinLimit) {
   if (threadIdx.x == 0 && *s_flag == 0) {
     const unsigned goal = nblocks * target;
     unsigned it = 0;
@@ -227,7 +227,7 @@ __device__ __forceinline__ bool grid_wait(unsigned* count, unsigned nblocks, uns
         break;
       }
       if (c >= goal) break;
-      if (++it > kSpinLimit) {
+      if (++it > limit) {
         set_status(status, ST_TIMEOUT);
         atomicOr(count, kBarPoison);
         *s_flag = 1;

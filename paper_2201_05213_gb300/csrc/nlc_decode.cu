@@ -25,6 +25,8 @@ struct DecodeArgs {
   long long n_times;
   unsigned long long seed;    // sampler only
   uint8_t* ring;              // sheared wavefront decoder: the units' sheared rings
+  unsigned spin_limit;        // polls of the grid barrier before a timeout
+  unsigned mma_limit;         // polls of an MMA completion before a timeout
 };
 
 // Threads of the decoder's CTA: the BF16 pipeline runs 16 warps (32 coding
@@ -188,7 +190,10 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
   extern __shared__ __align__(128) unsigned char smem[];
   const Dims& d = a.m.d;
   TileSmem t = carve(d, smem, a.n_units, NT / kGW, true);
-  if constexpr (PREC == PREC_BF16) tc_setup(t.tc);
+  if constexpr (PREC == PREC_BF16) {
+    tc_setup(t.tc);
+    t.tc.mma_limit = a.mma_limit;
+  }
   load_weights<PREC>(a.m, t);
   if (threadIdx.x == 0) t.flag[0] = 0;
   if (threadIdx.x < 16) t.pc[threadIdx.x] = 0;
@@ -318,14 +323,21 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       }
       if (pr) pc[5] += 1;
       tick(1);
+      bool net_ok;
       if constexpr (SHEAR) {
         const long long c0 = pc != nullptr && threadIdx.x == 0 ? clock64() : 0;
         tc_gather_shear_win(a.units, t.wrow, a.ring, d, t.tc, step, t.flag[3]);
         __syncthreads();
         if (pc != nullptr && threadIdx.x == 0) pc[13] += clock64() - c0;
-        tc_network<NT>(d, t.tc, t.flag[2], pc, true);
+        net_ok = tc_network<NT>(d, t.tc, t.flag[2], pc, true);
       } else {
-        tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+        net_ok = tile_network<PREC, true, NT>(a.m, a.units, t, n, pc);
+      }
+      // an MMA wait that timed out: record it and release every CTA from
+      // the grid barrier (this one leaves its loop at its next wait)
+      if (!net_ok && threadIdx.x == 0) {
+        set_status(a.status, ST_TIMEOUT);
+        atomicOr(a.bar, kBarPoison);
       }
       if constexpr (SAMPLE) {
         if (wide) sample_tile<32, NW, SHEAR>(a, t, n);
@@ -368,7 +380,7 @@ __global__ void __launch_bounds__(decode_threads<PREC>(), 1) decode_kernel(Decod
       tick(1);
     }
     if (G > 1) {
-      if (!grid_wait(a.bar, G, target, a.status, t.flag)) break;
+      if (!grid_wait(a.bar, G, target, a.status, t.flag, a.spin_limit)) break;
     } else {
       __syncthreads();
     }
@@ -449,6 +461,8 @@ cudaError_t launch_decode(const DeviceModel& m, const CodecBufs& b, const uint8_
   a.times = b.times;
   a.n_times = b.n_times;
   a.ring = b.ring;
+  a.spin_limit = b.spin_limit ? b.spin_limit : kSpinLimit;
+  a.mma_limit = b.mma_limit ? b.mma_limit : kMbarSpin;
   const bool win = b.ring != nullptr && sched == SCHED_WAVEFRONT;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
   const void* fn = decode_fn(m.d.prec, false, win);
@@ -484,6 +498,8 @@ cudaError_t launch_sample(const DeviceModel& m, const CodecBufs& b, int sched, i
   a.n_times = 0;
   a.seed = seed;
   a.ring = b.ring;
+  a.spin_limit = b.spin_limit ? b.spin_limit : kSpinLimit;
+  a.mma_limit = b.mma_limit ? b.mma_limit : kMbarSpin;
   const bool win = b.ring != nullptr && sched == SCHED_WAVEFRONT;
   const size_t smem = decode_smem_bytes(m.d, b.n_units);
   const void* fn = decode_fn(m.d.prec, true, win);

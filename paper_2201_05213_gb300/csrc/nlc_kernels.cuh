@@ -61,6 +61,8 @@ struct CodecBufs {
   unsigned long long* prof = nullptr;  // decoder phase cycle counters (16), optional
   unsigned long long* times = nullptr;  // decoder step end times, optional
   long long n_times = 0;
+  unsigned spin_limit = 0;  // decoder: polls of the grid barrier / an MMA completion before a
+  unsigned mma_limit = 0;   // timeout is recorded (0: the defaults)
 };
 
 // Launchers (return cudaError_t of the launch).

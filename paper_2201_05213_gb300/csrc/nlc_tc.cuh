@@ -111,6 +111,7 @@ struct TcSmem {
   uint32_t tmem;
   uint32_t phase;
   int ok;
+  unsigned mma_limit;  // polls of an MMA completion before a timeout is recorded
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -134,6 +135,7 @@ __device__ __forceinline__ TcSmem tc_carve(const Dims& d, unsigned char* smem) {
   t.tmem = 0;
   t.phase = 0;
   t.ok = 1;
+  t.mma_limit = kMbarSpin;
   return t;
 }
 
@@ -169,11 +171,27 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
       : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
-  for (unsigned it = 0; it < kMbarSpin; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase,
+                                          unsigned limit = kMbarSpin) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Non-blocking test of an mbarrier phase, at most `limit` times.
+__device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t phase, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(smem_u32(mbar)), "r"(phase)
@@ -582,8 +600,16 @@ __device__ __forceinline__ void tc_issue_ta(const TcSmem& t, uint32_t b_off, int
   }
 }
 
+// A wait that gives up after t.mma_limit polls reports the timeout, then
+// waits (bounded by the default limit) for the MMAs it issued, so that no
+// tensor-core write is in flight when the caller goes on or frees its
+// tensor memory.
 __device__ __forceinline__ bool tc_wait(TcSmem& t) {
-  bool ok = mbar_wait(t.mbar, t.phase);
+  // a reduced limit counts non-blocking tests (a blocking try_wait may
+  // itself suspend until the phase completes)
+  bool ok = t.mma_limit >= kMbarSpin ? mbar_wait(t.mbar, t.phase)
+                                     : mbar_test(t.mbar, t.phase, t.mma_limit);
+  if (!ok) mbar_wait(t.mbar, t.phase);
   t.phase ^= 1u;
   fence_after_sync();
   return ok;

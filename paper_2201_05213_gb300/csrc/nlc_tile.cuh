@@ -312,8 +312,9 @@ __device__ __forceinline__ void load_weights(const DeviceModel& m, TileSmem& t) 
 // gather + network for the slots of the tile; P[m][NOp] lands in t.U0.
 // With pc non-null (BF16), thread 0 adds its gather cycles to pc[13] and the
 // network's sub-phases to pc[14], pc[15] (shared-memory accumulators).
+// Returns false (in every thread) if an MMA completion wait timed out.
 template <int PREC, bool kCoherent, int NT = kThreads>
-__device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* units, TileSmem& t,
+__device__ __forceinline__ bool tile_network(const DeviceModel& m, const Unit* units, TileSmem& t,
                                              int n_valid, long long* pc = nullptr) {
   if constexpr (PREC == PREC_BF16) {
     const long long c0 = pc != nullptr && threadIdx.x == 0 ? clock64() : 0;
@@ -321,11 +322,12 @@ __device__ __forceinline__ void tile_network(const DeviceModel& m, const Unit* u
     else tc_gather<kCoherent>(units, t.slots, m.d, t.tc, n_valid);
     __syncthreads();
     if (pc != nullptr && threadIdx.x == 0) pc[13] += clock64() - c0;
-    tc_network<NT>(m.d, t.tc, n_valid, pc);
+    return tc_network<NT>(m.d, t.tc, n_valid, pc);
   } else {
     gather_f32<kMT, kCoherent>(units, t.slots, m.d.h, t.U0);
     __syncthreads();
     network_simt_run<kMT>(m.d, t.Wt, t.A, t.B1, t.U0);
+    return true;
   }
 }
 

@@ -40,7 +40,7 @@ EXPORTS = [
     "nlc_compress_noalloc", "nlc_decode_profile",
     "nlc_plan_decode", "nlc_plan_run", "nlc_plan_tune", "nlc_plan_destroy",
     "nlc_decode_step_times", "nlc_measure_mufu", "nlc_backward", "nlc_load_weights",
-    "nlc_sample",
+    "nlc_sample", "nlc_set_wait_limits",
 ]
 
 
@@ -103,6 +103,7 @@ def load():
             L.nlc_backward.argtypes = [p, p, i, i, i, p, p, p]
             L.nlc_load_weights.argtypes = [p, p, sz, p]
             L.nlc_sample.argtypes = [p, p, i, i, C.c_uint64, i, p]
+            L.nlc_set_wait_limits.argtypes = [p, C.c_uint32, C.c_uint32]
             for name in EXPORTS:
                 getattr(L, name).restype = getattr(L, name).restype or i
             L.nlc_last_error.restype = C.c_char_p
@@ -328,3 +329,8 @@ def nlc_sample(ctx, outs, patch, seed, schedule, stream=None):
     arr, n = _images(outs), len(outs)
     _check(load().nlc_sample(ctx, arr, n, patch, int(seed) & 0xFFFFFFFFFFFFFFFF, schedule,
                              _stream(stream)))
+
+
+def nlc_set_wait_limits(ctx, grid_polls=0, mma_polls=0):
+    """Polls of the decoder's bounded waits before a timeout (0 = defaults)."""
+    _check(load().nlc_set_wait_limits(ctx, int(grid_polls), int(mma_polls)))

@@ -278,3 +278,24 @@ def test_step_times_give_image_latencies():
     assert t[0] > 0 and (np.diff(t[:T + 1]) >= 0).all() and (t[T + 1:] == 0).all()
     lat = [t[s] - t[0] for s in steps]
     assert lat[1] <= lat[2] <= lat[0] and lat[0] == t[T] - t[0]
+
+
+@pytest.mark.parametrize("prec", [N.NLC_BF16, N.NLC_BF16_SHEARED])
+def test_bounded_waits_report_timeouts_and_the_context_recovers(prec):
+    # The decoder's waits are bounded: a grid-barrier wait or an MMA
+    # completion wait that gives up records NLC_ERR_TIMEOUT and releases every
+    # CTA; the launch ends and the context decodes again with normal limits.
+    codec, _ = make_codec((3, 32, 1, 10), prec, seed=50)
+    sizes = [(48, 48)] * 4
+    imgs = images(51, sizes)
+    d = [to_dev(i) for i in imgs]
+    data, offs = codec.compress(d, 16, N.NLC_LAYOUT_ROW)
+    N.nlc_set_tuning(codec.ctx, 1, 0)  # one pixel per CTA and step: many CTAs meet each step
+    for grid_polls, mma_polls in ((1, 0), (0, 1)):
+        N.nlc_set_wait_limits(codec.ctx, grid_polls, mma_polls)
+        codec.decompress(data, offs, sizes, 16, N.NLC_LAYOUT_ROW, check=False)
+        assert N.nlc_sync_status(codec.ctx) == N.NLC_ERR_TIMEOUT, (grid_polls, mma_polls)
+        N.nlc_set_wait_limits(codec.ctx, 0, 0)
+        outs = codec.decompress(data, offs, sizes, 16, N.NLC_LAYOUT_ROW)
+        for o, i in zip(outs, imgs):
+            assert np.array_equal(o.cpu().numpy(), i)
