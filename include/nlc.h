@@ -196,10 +196,12 @@ int nlc_compress_bound(const int32_t* h_H, const int32_t* h_W, int n, int patch,
 
 /* Compresses n images.  Container i is written to d_out + d_offsets[i] and
  * ends at d_offsets[i+1]; d_offsets (n+1 uint64, device) is written by the
- * library.  Container: 32-byte header ("NLC1", version, h, layout,
- * precision, H, W, patch, n_streams, weight hash), n_streams uint32 stream
- * lengths, the streams (rANS, 4-byte big-endian final state then bytes),
- * zero padding to 16 bytes.  If the total exceeds `cap` nothing is written
+ * library.  Container: 32-byte header ("NLC1", version 2, h, layout,
+ * precision, H, W, patch, n_streams, weight hash), n_streams stream lengths
+ * (uint16 when 6 x the pixels of the image's largest stream + 4 < 2^16 --
+ * a row of at most 10,921 pixels with one stream per row -- else uint32),
+ * the streams (rANS, 4-byte big-endian final state then bytes), zero padding
+ * to 16 bytes.  If the total exceeds `cap` nothing is written
  * and the device status becomes NLC_ERR_CAPACITY (d_offsets still holds the
  * sizes).  The encoder computes every pixel's frequency tables in parallel
  * with the decoder's own device code (the paper's encoder reruns the

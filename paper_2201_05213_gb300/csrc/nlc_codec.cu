@@ -235,8 +235,8 @@ __global__ void unit_sum_kernel(const Unit* __restrict__ units, int n_units, int
 
 // Container plan (one thread): offsets of the containers and of the units'
 // stream data; flags a capacity overflow.
-__global__ void pack_plan_kernel(const ImageRec* __restrict__ images, int n_images,
-                                 const unsigned long long* __restrict__ unit_bytes,
+__global__ void pack_plan_kernel(const ImageRec* __restrict__ images, int n_images, int layout,
+                                 int patch, const unsigned long long* __restrict__ unit_bytes,
                                  unsigned long long* __restrict__ unit_off,
                                  unsigned long long* __restrict__ offsets, unsigned long long cap,
                                  int* status) {
@@ -244,7 +244,8 @@ __global__ void pack_plan_kernel(const ImageRec* __restrict__ images, int n_imag
   unsigned long long off = 0;
   for (int i = 0; i < n_images; i++) {
     const ImageRec I = images[i];
-    unsigned long long o = off + kHeaderBytes + 4ull * I.n_streams;
+    const int lw = len_width(I.H, I.W, patch, layout);
+    unsigned long long o = off + kHeaderBytes + (unsigned long long)lw * I.n_streams;
     for (int u = I.unit_base; u < I.unit_base + I.n_units; u++) {
       unit_off[u] = o;
       o += unit_bytes[u];
@@ -282,7 +283,11 @@ __global__ void pack_copy_kernel(DeviceModel m, const Unit* __restrict__ units, 
     if (k < ns) {
       soff[U.stream_base + k] = unit_off[u] + (unsigned long long)(run + ex);
       const int sidx = U.stream_base + k - I.stream_base;
-      *reinterpret_cast<uint32_t*>(out + cbase + kHeaderBytes + 4ull * sidx) = (uint32_t)len;
+      uint8_t* lp = out + cbase + kHeaderBytes;
+      if (len_width(I.H, I.W, patch, layout) == 2)
+        reinterpret_cast<uint16_t*>(lp)[sidx] = (uint16_t)len;
+      else
+        reinterpret_cast<uint32_t*>(lp)[sidx] = (uint32_t)len;
     }
     run += total;
   }
@@ -356,8 +361,8 @@ cudaError_t launch_encode(const DeviceModel& m, const CodecBufs& b, int layout, 
         b.units, b.n_units, layout, b.lens, b.unit_bytes);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  pack_plan_kernel<<<1, 32, 0, s>>>(b.images, b.n_images, b.unit_bytes, b.unit_off, d_offsets, cap,
-                                    b.status);
+  pack_plan_kernel<<<1, 32, 0, s>>>(b.images, b.n_images, layout, patch, b.unit_bytes, b.unit_off,
+                                    d_offsets, cap, b.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (b.n_units > 0) {
     pack_copy_kernel<<<b.n_units, 256, 0, s>>>(m, b.units, b.n_units, b.images, b.n_images, layout,
@@ -385,7 +390,8 @@ __global__ void parse_header_kernel(DeviceModel m, const ImageRec* __restrict__ 
   const ImageRec I = images[i];
   const unsigned long long o = offsets[i], o1 = offsets[i + 1];
   int err = 0;
-  if (o1 < o || o1 - o < kHeaderBytes + 4ull * I.n_streams || (o & 15ull)) {
+  const int lw = len_width(I.H, I.W, patch, layout);
+  if (o1 < o || o1 - o < kHeaderBytes + (unsigned long long)lw * I.n_streams || (o & 15ull)) {
     err = ST_CORRUPT;
   } else {
     const uint8_t* h = in + o;
@@ -403,7 +409,7 @@ __global__ void parse_header_kernel(DeviceModel m, const ImageRec* __restrict__ 
 }
 
 __global__ void parse_lens_kernel(const Unit* __restrict__ units, int n_units,
-                                  const ImageRec* __restrict__ images, int layout,
+                                  const ImageRec* __restrict__ images, int layout, int patch,
                                   const uint8_t* __restrict__ in,
                                   const unsigned long long* __restrict__ offsets,
                                   const int* __restrict__ bad, int32_t* __restrict__ lens,
@@ -414,12 +420,15 @@ __global__ void parse_lens_kernel(const Unit* __restrict__ units, int n_units,
   const ImageRec I = images[U.image];
   const int ns = unit_streams(U, layout);
   const bool ok = bad[U.image] == 0;
+  const int lw = len_width(I.H, I.W, patch, layout);
   unsigned long long s = 0;
   for (int k = lane; k < ns; k += 32) {
     const int sidx = U.stream_base + k - I.stream_base;
-    uint32_t len = ok ? *reinterpret_cast<const uint32_t*>(in + offsets[U.image] + kHeaderBytes +
-                                                           4ull * sidx)
-                      : 0u;
+    const uint8_t* lp = in + offsets[U.image] + kHeaderBytes;
+    uint32_t len = 0u;
+    if (ok)
+      len = lw == 2 ? (uint32_t)reinterpret_cast<const uint16_t*>(lp)[sidx]
+                    : reinterpret_cast<const uint32_t*>(lp)[sidx];
     lens[U.stream_base + k] = (int32_t)len;
     s += len;
   }
@@ -428,15 +437,16 @@ __global__ void parse_lens_kernel(const Unit* __restrict__ units, int n_units,
   if (lane == 0) unit_bytes[u] = s;
 }
 
-__global__ void parse_plan_kernel(const ImageRec* __restrict__ images, int n_images,
-                                  const unsigned long long* __restrict__ offsets,
+__global__ void parse_plan_kernel(const ImageRec* __restrict__ images, int n_images, int layout,
+                                  int patch, const unsigned long long* __restrict__ offsets,
                                   const unsigned long long* __restrict__ unit_bytes,
                                   unsigned long long* __restrict__ unit_off, int* __restrict__ bad,
                                   int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = 0; i < n_images; i++) {
     const ImageRec I = images[i];
-    unsigned long long o = offsets[i] + kHeaderBytes + 4ull * I.n_streams;
+    unsigned long long o = offsets[i] + kHeaderBytes +
+                           (unsigned long long)len_width(I.H, I.W, patch, layout) * I.n_streams;
     for (int u = I.unit_base; u < I.unit_base + I.n_units; u++) {
       unit_off[u] = o;
       o += unit_bytes[u];
@@ -509,10 +519,10 @@ cudaError_t launch_parse(const DeviceModel& m, const CodecBufs& b, const uint8_t
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (b.n_units == 0) return cudaSuccess;
   parse_lens_kernel<<<grid_for((long long)b.n_units * 32, 256, 1 << 20), 256, 0, s>>>(
-      b.units, b.n_units, b.images, layout, in, d_offsets, bad, b.lens, b.unit_bytes);
+      b.units, b.n_units, b.images, layout, patch, in, d_offsets, bad, b.lens, b.unit_bytes);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  parse_plan_kernel<<<1, 32, 0, s>>>(b.images, b.n_images, d_offsets, b.unit_bytes, b.unit_off,
-                                     bad, b.status);
+  parse_plan_kernel<<<1, 32, 0, s>>>(b.images, b.n_images, layout, patch, d_offsets, b.unit_bytes,
+                                     b.unit_off, bad, b.status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   parse_streams_kernel<<<b.n_units, 256, 0, s>>>(b.units, b.n_units, layout, in, b.lens,
                                                  b.unit_off, bad, b.st,

@@ -20,8 +20,20 @@ struct ImageRec {
 // stream lengths in bytes, then the streams back to back; the container is
 // zero-padded to a multiple of 16 bytes.
 constexpr uint32_t kMagic = 0x31434C4Eu;  // "NLC1"
-constexpr int kVersion = 1;
+constexpr int kVersion = 2;
 constexpr int kHeaderBytes = 32;
+
+// Bytes per entry of a container's stream-length table: 2 when no stream of
+// the image can reach 2^16 bytes (a pixel codes to at most 6 bytes, a
+// stream adds 4: 6 px + 4 < 2^16 for the largest stream of the image's
+// geometry), else 4.  A function of (H, W, patch, layout) alone, so the
+// decoder derives it from the header.
+__host__ __device__ __forceinline__ int len_width(int H, int W, int patch, int layout) {
+  const long long P = patch > 0 ? patch : (H > W ? H : W);
+  const long long w = W < P ? W : P, hh = H < P ? H : P;
+  const long long px = layout == 1 ? w : hh * w;
+  return 6 * px + 4 < 65536 ? 2 : 4;
+}
 
 struct DeviceModel {
   Dims d;

@@ -120,7 +120,7 @@ def test_code_length_matches_oracle(prec, tol):
     cum = codec.tables(P, pix)
     ideal = CD.ideal_bits_from_tables(cum, pix)
     nstreams = sum(i.shape[0] for i in imgs)
-    payload = int(offs[-1]) - sum(32 + 4 * i.shape[0] for i in imgs)
+    payload = int(offs[-1]) - sum(32 + _len_width(*i.shape[:2], 0, 1) * i.shape[0] for i in imgs)
     assert 8 * payload <= ideal + 32 * nstreams + 8 * 16 * len(imgs)
     assert 8 * payload >= ideal - 1
 
@@ -185,7 +185,7 @@ def test_oracle_decodes_same_partition_same_pixels():
     outs = codec.decompress(data, offs, [(32, 32)], 0, 0, N.NLC_SCHED_SEQUENTIAL)
     assert np.array_equal(outs[0].cpu().numpy(), dec)
     # one stream each: the payloads differ only through FP32 vs FP64 tables
-    assert abs((int(offs[1]) - 36) - len(words)) <= 16
+    assert abs((int(offs[1]) - 32 - _len_width(32, 32, 0, 0)) - len(words)) <= 16
     assert 8 * len(words) <= bq + 32 + 1
 
 
@@ -207,13 +207,38 @@ def test_streams_equal_oracle_rans_on_gpu_tables(prec):
     start = cum[px, ch, v]
     freq = cum[px, ch, v + 1] - start
     buf = data.cpu().numpy()[int(offs[0]):int(offs[1])]
-    lens = buf[32:32 + 4 * H].copy().view("<u4")
-    pos = 32 + 4 * H
+    assert _len_width(H, W, 0, 1) == 2
+    lens = buf[32:32 + 2 * H].copy().view("<u2")
+    pos = 32 + 2 * H
     for r in range(H):
         rows = slice(r * W, (r + 1) * W)
         ref = O.rans_encode(start[rows].reshape(-1), freq[rows].reshape(-1))
         assert np.array_equal(buf[pos:pos + int(lens[r])], ref), r
         pos += int(lens[r])
+
+
+def _len_width(H, W, patch, layout):
+    """Bytes per stream-length entry of a container (include/nlc.h): 2 when
+    6 x (pixels of the image's largest stream) + 4 < 2^16, else 4."""
+    P = patch if patch > 0 else max(H, W)
+    px = min(W, P) if layout == 1 else min(H, P) * min(W, P)
+    return 2 if 6 * px + 4 < 65536 else 4
+
+
+def test_wide_rows_use_four_byte_lengths():
+    # rows of 11000 pixels can exceed 2^16 bytes: 4-byte length entries
+    codec, _ = make_codec((1, 16, 0, 2), N.NLC_BF16, seed=60)
+    sizes = [(3, 11000), (5, 7)]
+    imgs = images(61, sizes)
+    d = [to_dev(i) for i in imgs]
+    data, offs = codec.compress(d, 0, 1)
+    assert _len_width(3, 11000, 0, 1) == 4 and _len_width(5, 7, 0, 1) == 2
+    lens = data.cpu().numpy()[int(offs[0]) + 32:int(offs[0]) + 32 + 12].copy().view("<u4")
+    assert int(offs[0]) + 32 + 12 + int(lens.sum()) <= int(offs[1])
+    for sched in (N.NLC_SCHED_WAVEFRONT, N.NLC_SCHED_RASTER):
+        outs = codec.decompress(data, offs, sizes, 0, 1, sched)
+        for o, i in zip(outs, imgs):
+            assert np.array_equal(o.cpu().numpy(), i)
 
 
 def _check_increasing(cum):
