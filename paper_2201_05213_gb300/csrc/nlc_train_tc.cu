@@ -57,7 +57,7 @@ constexpr int kLbStride = kMaxK + 1;  // per-row table of l_k (odd: rows on diff
 // arithmetic, so that no offset table has to live in local memory.
 struct TTPlan {
   int w0, w1, wstride, wh;  // BF16 weight tiles (the decoder's layout)
-  int bias, ones, u, gx, g2, xe, red, slots, mbar, tslot, end;
+  int bias, ones, u, gx, g2, xe, red, slots, taps, mbar, tslot, end;
   bool fits;
 };
 
@@ -103,6 +103,8 @@ __host__ __device__ inline TTPlan tt_plan(const Dims& d) {
   o = align_up(o, 16);
   p.slots = o;  // (image, i, j, valid) per pixel
   o += kTTM * 16;
+  p.taps = o;  // (dy, dx) of the context taps (Eq. 3), 2h(h+1) <= 24
+  o += 24 * 8;
   p.mbar = o;
   o += 8;
   p.tslot = o;
@@ -181,25 +183,24 @@ __device__ __forceinline__ float elu_d_from_act(float u) { return u > 0.f ? 1.f 
 
 // X tile [128][Fp] (K-major): feature 3p + c of pixel m = 2v - 255 of channel
 // c of context tap p (Eq. 3), 0 outside the image and for F <= k < Fp and for
-// rows past the batch.
-__device__ __noinline__ void tt_gather(const Dims& d, const uint8_t* __restrict__ batch, int H, int W,
-                          long long n_px, long long q0, unsigned char* X) {
-  const int ntap = d.F / 3, Fp = d.Fp, h = d.h;
+// rows past the batch.  Pixel m's (image, row, column, valid) come from the
+// tile's slot table and tap p's offsets from taps[p], so that no index is
+// divided per feature; thread t handles pixel t mod 128.
+__device__ __noinline__ void tt_gather(const Dims& d, const uint8_t* __restrict__ batch, int H,
+                                       int W, const int4* slots, const int2* taps,
+                                       unsigned char* X) {
+  const int ntap = d.F / 3, Fp = d.Fp;
   uint16_t* x = reinterpret_cast<uint16_t*>(X);
-  const int HW = H * W;  // the batch has fewer than 2^27 pixels
-  for (int it = threadIdx.x; it < kTTM * (Fp / 3 + 1); it += blockDim.x) {
-    const int m = it % kTTM, p = it / kTTM;
-    if (3 * p >= Fp) continue;
-    const long long q = q0 + m;
+  const int m = threadIdx.x & (kTTM - 1);
+  const int4 sl = slots[m];
+  const long long base = ((long long)sl.x * H) * W;
+  for (int p = threadIdx.x / kTTM; 3 * p < Fp; p += kTT / kTTM) {
     float v[3] = {0.f, 0.f, 0.f};
-    if (q < n_px && p < ntap) {
-      const int qi = (int)q, n = qi / HW, rr = qi % HW;
-      const int i = rr / W, j = rr % W;
-      int dy, dx;
-      tap_offset(p, h, dy, dx);
-      const int ii = i + dy, jj = j + dx;
+    if (sl.w != 0 && p < ntap) {
+      const int2 t = taps[p];
+      const int ii = sl.y + t.x, jj = sl.z + t.y;
       if (ii >= 0 && ii < H && jj >= 0 && jj < W) {
-        const uint8_t* px = batch + ((long long)n * HW + (long long)ii * W + jj) * 3;
+        const uint8_t* px = batch + (base + (long long)ii * W + jj) * 3;
         v[0] = (float)(2 * (int)px[0] - 255);
         v[1] = (float)(2 * (int)px[1] - 255);
         v[2] = (float)(2 * (int)px[2] - 255);
@@ -370,8 +371,8 @@ __device__ __noinline__ float tt_likelihood(const Dims& d, uint32_t tcol, const 
     float mx = -INFINITY;
     for (int k = 0; k < K; k++) mx = fmaxf(mx, lb[k]);
     float se = 0.f;
-    for (int k = 0; k < K; k++) se = __fadd_rn(se, expf(__fsub_rn(lb[k], mx)));
-    return __fadd_rn(mx, logf(se));
+    for (int k = 0; k < K; k++) se = __fadd_rn(se, exp_f(__fsub_rn(lb[k], mx)));
+    return __fadd_rn(mx, log_f(se));
   };
   if (MODE == 0) {
     const int v[3] = {valid ? (int)px[0] : 0, valid ? (int)px[1] : 0, valid ? (int)px[2] : 0};
@@ -405,27 +406,42 @@ __device__ __noinline__ float tt_likelihood(const Dims& d, uint32_t tcol, const 
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         const float ls = fmaxf(pr[4 + c], -7.f);
-        const float inv = expf(-ls), mc = m3[c];
+        const float inv = exp_f(-ls), mc = m3[c];
         if (!want_d) {
           lk = __fadd_rn(lk, log_bin_mass_f(mc, inv, bin_log_width(ls, inv), v[c]));
           continue;
         }
+        // sigma(-a) = 1/(1 + e^a), sigma(b) = 1/(1 + e^-b) through the MUFU
+        // (a gradient, not a frequency table: the approximations only
+        // perturb it by ~1e-6 relative)
         if (v[c] == 0) {
           const float aa = __fmul_rn(__fsub_rn(edge_f(1), mc), inv);
-          const float sa = 1.f / (1.f + expf(aa));
+          const float sa = rcp_approx(__fadd_rn(1.f, exp_f(aa)));
           dlm[c] = -inv * sa;
           dll[c] = -aa * sa;
         } else if (v[c] == 255) {
           const float bb = __fmul_rn(__fsub_rn(edge_f(255), mc), inv);
-          const float sb = 1.f / (1.f + expf(-bb));
+          const float sb = rcp_approx(__fadd_rn(1.f, exp_f(-bb)));
           dlm[c] = inv * sb;
           dll[c] = bb * sb;
         } else {
           const float aa = __fmul_rn(__fsub_rn(edge_f(v[c] + 1), mc), inv);
           const float bb = __fmul_rn(__fsub_rn(edge_f(v[c]), mc), inv);
-          const float dd = __fmul_rn(__fdiv_rn(2.f, 255.f), inv);
-          const float gk = 1.f / expm1f(dd);
-          const float sa = 1.f / (1.f + expf(aa)), sb = 1.f / (1.f + expf(-bb));
+          const float dd = __fmul_rn(2.f / 255.f, inv);
+          // 1/(e^d - 1): Taylor series of e^d - 1 for d < 1/8 (no cancellation)
+          float em1;
+          if (dd < 0.125f) {
+            float p = __fmaf_rn(dd, 1.f / 120.f, 1.f / 24.f);
+            p = __fmaf_rn(p, dd, 1.f / 6.f);
+            p = __fmaf_rn(p, dd, 0.5f);
+            p = __fmaf_rn(p, dd, 1.f);
+            em1 = __fmul_rn(dd, p);
+          } else {
+            em1 = __fsub_rn(exp_f(dd), 1.f);
+          }
+          const float gk = rcp_approx(em1);
+          const float sa = rcp_approx(__fadd_rn(1.f, exp_f(aa)));
+          const float sb = rcp_approx(__fadd_rn(1.f, exp_f(-bb)));
           dlm[c] = -inv * (sa - sb);
           dll[c] = -aa * sa + bb * sb - gk * dd;
         }
@@ -448,8 +464,8 @@ __device__ __noinline__ float tt_likelihood(const Dims& d, uint32_t tcol, const 
       float pr[10], co[3], dlm[3], dll[3];
       load_comp(k, pr);
       comp_terms(pr, co, dlm, dll, true);
-      const float rho = valid ? expf(__fsub_rn(lb[k], lse)) : 0.f;
-      const float pi = expf(__fsub_rn(pr[0], lse_pi));
+      const float rho = valid ? exp_f(__fsub_rn(lb[k], lse)) : 0.f;
+      const float pi = exp_f(__fsub_rn(pr[0], lse_pi));
       float gk[10];
       gk[0] = sc * (pi - rho);
       const float dmR = -rho * dlm[0], dmG = -rho * dlm[1], dmB = -rho * dlm[2];
@@ -501,6 +517,12 @@ __global__ void __launch_bounds__(kTT, 1)
   float* sbias = reinterpret_cast<float*>(sm + pl.bias);
   float* red = reinterpret_cast<float*>(sm + pl.red);
   int4* slots = reinterpret_cast<int4*>(sm + pl.slots);
+  int2* taps = reinterpret_cast<int2*>(sm + pl.taps);
+  for (int p = threadIdx.x; p < d.F / 3; p += blockDim.x) {
+    int dy, dx;
+    tap_offset(p, d.h, dy, dx);
+    taps[p] = make_int2(dy, dx);
+  }
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + pl.mbar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + pl.tslot);
   // weights (BF16 tiles) and biases
@@ -574,7 +596,8 @@ __global__ void __launch_bounds__(kTT, 1)
       }
       slots[threadIdx.x] = sv;
     }
-    tt_gather(d, batch, H, W, n_px, q0, sm + pl.gx);
+    __syncthreads();  // the slots (and, on the first tile, the taps)
+    tt_gather(d, batch, H, W, slots, taps, sm + pl.gx);
     sync_for_mma();
 
     // ---------------- forward ----------------
@@ -662,7 +685,7 @@ __global__ void __launch_bounds__(kTT, 1)
     }
     if (!ok) break;
     // first layer: dW0 = da_0^T X / 255 (X gathered again), db0 = da_0^T 1
-    tt_gather(d, batch, H, W, n_px, q0, sm + pl.xe);
+    tt_gather(d, batch, H, W, slots, taps, sm + pl.xe);
     sync_for_mma();
     if (threadIdx.x == 0) {
       tt_mma(tmem + kColDW, op_mn(s0 + pl.gx, C), true, op_mn(s0 + pl.xe, Fp), true, Fp,
