@@ -59,17 +59,23 @@ def workload_name():
 # DRAM traffic of decode_kernel per decoded pixel from one ncu capture of the
 # small case at 16 CTAs (1x1024^2: 5.96 MB read + 0.35 MB written for
 # 1,048,576 px), scaled to a launch by its pixels.  It holds only for the
-# kernel sources it was taken on: TRAFFIC_SRC_SHA is their sha256, and any
-# other sources report null.
+# kernel sources it was taken on: TRAFFIC_SRC_SHA is the sha256 of
+# DECODER_SOURCES, and any other sources report null.
 TRAFFIC_B_PER_PX = 6.02
 TRAFFIC_SRC_SHA = "b4304dcf8554dd3198b9326133be9653242df28a16d1a72a7609e43c5e08feb5"
+
+
+# the sources decode_kernel is compiled from
+DECODER_SOURCES = ["nlc_decode.cu", "nlc_tile.cuh", "nlc_tc.cuh", "nlc_model.cuh",
+                   "nlc_common.cuh", "nlc_kernels.cuh"]
 
 
 def _csrc_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2201_05213_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(f).encode())
+    for name in DECODER_SOURCES:
+        f = os.path.join(ROOT, "paper_2201_05213_gb300", "csrc", name)
+        h.update(name.encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
