@@ -643,29 +643,29 @@ namespace nlc {
 
 // ---------------------------------------------------------------------
 // Device check behind the pointwise CDF: ex2.approx must be non-decreasing
-// on [-126, 126] and rcp.approx non-increasing on [1, 2^127).  Every pair of
-// adjacent floats in those ranges is compared (3.3e9 pairs, about a
-// millisecond); viol receives the number of pairs out of order.
+// over all floats (-inf .. +inf) and rcp.approx non-increasing on [1, +inf].
+// Every pair of adjacent floats in those ranges is compared (5.4e9 pairs,
+// a few milliseconds); viol receives the number of pairs out of order.
 // ---------------------------------------------------------------------
 __global__ void mono_check_kernel(unsigned long long* viol) {
-  constexpr uint32_t kB126 = 0x42FC0000u;  // bit pattern of 126.0f
-  constexpr uint32_t kOne = 0x3F800000u, kTop = 0x7F000000u;
+  constexpr uint32_t kInf = 0x7F800000u;  // bit pattern of +inf
+  constexpr uint32_t kOne = 0x3F800000u;
   // ranges of bit patterns b, each compared with b + 1:
-  //   [0, kB126): x = +0 .. 126, ex2 non-decreasing
-  //   [kB126, 2 kB126): x = -0 .. -126 (value falls as bits rise), ex2 non-increasing
-  //   [2 kB126, 2 kB126 + kTop - kOne): x = 1 .. 2^127, rcp non-increasing
-  const unsigned long long n = 2ull * kB126 + (kTop - kOne);
+  //   [0, kInf): x = +0 .. +inf, ex2 non-decreasing
+  //   [kInf, 2 kInf): x = -0 .. -inf (value falls as bits rise), ex2 non-increasing
+  //   [2 kInf, 2 kInf + kInf - kOne): x = 1 .. +inf, rcp non-increasing
+  const unsigned long long n = 2ull * kInf + (kInf - kOne);
   unsigned long long bad = 0;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    if (i < kB126) {
+    if (i < kInf) {
       const uint32_t b = (uint32_t)i;
       bad += ex2_approx(__uint_as_float(b + 1)) < ex2_approx(__uint_as_float(b)) ? 1 : 0;
-    } else if (i < 2ull * kB126) {
-      const uint32_t b = 0x80000000u | (uint32_t)(i - kB126);
+    } else if (i < 2ull * kInf) {
+      const uint32_t b = 0x80000000u | (uint32_t)(i - kInf);
       bad += ex2_approx(__uint_as_float(b + 1)) > ex2_approx(__uint_as_float(b)) ? 1 : 0;
     } else {
-      const uint32_t b = kOne + (uint32_t)(i - 2ull * kB126);
+      const uint32_t b = kOne + (uint32_t)(i - 2ull * kInf);
       bad += rcp_approx(__uint_as_float(b + 1)) > rcp_approx(__uint_as_float(b)) ? 1 : 0;
     }
   }

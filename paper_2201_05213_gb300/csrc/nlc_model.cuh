@@ -290,6 +290,9 @@ struct TableScratch {
 // they move 65280 F(b) by at most half a count per component.
 constexpr float kWmin = 7.62939453125e-06f;
 
+// Bound of a component's location in the CDF (2^100; |m - e| c stays finite).
+constexpr float kMMax = 1.2676506002282294e30f;
+
 // Fixed point with 23 fraction bits: x in [0, 2^23] plus 2^23, rounded to
 // nearest, is 2^23 + rint(x) (the spacing of floats in [2^23, 2^24] is 1);
 // its bit pattern minus that of 2^23 is rint(x).
@@ -330,7 +333,9 @@ __device__ __forceinline__ unsigned grp_mask(int lane) {
 // warp uses redux.sync (the maximum on order-preserving integer keys:
 // negative floats get their magnitude bits flipped); a 16-lane group uses
 // xor butterflies, because redux.sync with a mask per half warp is slower
-// than the butterfly.  Both forms give the same value.
+// than the butterfly.  Both forms give the same value for inputs that are
+// not NaN (the integer keys would rank a NaN above +inf, fmaxf drops it), so
+// the callers map NaN to -inf first (no_nan).
 template <int GW>
 __device__ __forceinline__ float grp_max_r(float v) {
   if constexpr (GW == 32) {
@@ -342,6 +347,7 @@ __device__ __forceinline__ float grp_max_r(float v) {
     return grp_max<GW>(v);
   }
 }
+__device__ __forceinline__ float no_nan(float v) { return v == v ? v : -INFINITY; }
 template <int GW>
 __device__ __forceinline__ uint32_t grp_isum(uint32_t v) {
   if constexpr (GW == 32) {
@@ -385,7 +391,7 @@ template <int GW = 32>
 __device__ __forceinline__ void comp_init(const float* P, int K, int gl, CompState& cs) {
   // log-sum-exp of the logits: exact max, then the sum of e^{logit - max}
   // in fixed point (an exact integer sum, S >= 2^23 from the max itself)
-  const float logit = gl < K ? P[gl] : -INFINITY;
+  const float logit = gl < K ? no_nan(P[gl]) : -INFINITY;  // a NaN logit: weight 0
   const float mx = grp_max_r<GW>(logit);
   const uint32_t E = fix23(gl < K ? exp_f(__fsub_rn(logit, mx)) : 0.f);
   const uint32_t S = grp_isum<GW>(E);
@@ -424,41 +430,45 @@ __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, i
 // Pointwise quantised CDF.  F(b) is a fixed-point number in units of 2^-23:
 // the sum over the active components of rint(w_k 2^23 sigmoid((e_b-m_k)/s_k)).
 // Every operation from b to a term is non-decreasing in b: correctly
-// rounded arithmetic with fixed operands, clamps, rint, and the MUFU
-// approximations ex2.approx (on [-126, 126]) and rcp.approx (on [1, 2^127)),
-// which are monotone on sm_103 (checked exhaustively over those ranges by
-// the library before a context is created, see mono_check_kernel).  So F is
-// non-decreasing in b as computed, the running max of the quantiser leaves q
-// unchanged, and each cum_b follows from b alone.  Integer sums do not
-// depend on the order of their terms: every split of the components over
-// lanes, in the encoder, the decoder or the table entry point, gives the
-// same cum_b.
+// rounded arithmetic with fixed operands, rint, and the MUFU approximations
+// ex2.approx (over all floats, saturating to +0 and +inf) and rcp.approx (on
+// [1, +inf]), which are monotone on sm_103 (checked exhaustively over those
+// ranges by the library before a context is created, see
+// mono_check_kernel).  So F is non-decreasing in b as computed, the running
+// max of the quantiser leaves q unchanged, and each cum_b follows from b
+// alone.  Integer sums do not depend on the order of their terms: every
+// split of the components over lanes, in the encoder, the decoder or the
+// table entry point, gives the same cum_b.
 // ---------------------------------------------------------------------
-constexpr float kZMax = 126.f;  // |z| clamp of the logistic's 2^z
 
 // One component's term of F at boundary value e: the logistic is
-// 1/(1 + 2^z) with z = (m - e) log2(e)/s clamped to [-126, 126], and
-// x = w 2^23 sigmoid lies in [0, 2^23]; x + 2^23 rounded to nearest is
-// 2^23 + rint(x) (float spacing 1 in [2^23, 2^24]), read back from its bits.
+// 1/(1 + 2^z) with z = (m - e) log2(e)/s (no clamp: a z beyond the float
+// range of 2^z gives 2^z = +inf or +0, hence the term's limits 0 and w), and
+// the fused w sigmoid + 2^23, rounded once to nearest, is 2^23 + rint(w 2^23
+// sigmoid) (w 2^23 sigmoid lies in [0, 2^23], float spacing 1 in [2^23,
+// 2^24]), read back from its bits.
 __device__ __forceinline__ uint32_t cdf_term(float e, const float4& p) {
-  const float z = fminf(fmaxf(__fmul_rn(__fsub_rn(p.x, e), p.y), -kZMax), kZMax);
-  const float x = __fmul_rn(p.z, rcp_approx(__fadd_rn(1.f, ex2_approx(z))));
-  return (uint32_t)__float_as_int(__fadd_rn(x, kFixOne)) - kFixOneBits;
+  const float z = __fmul_rn(__fsub_rn(p.x, e), p.y);
+  const float y = __fmaf_rn(p.z, rcp_approx(__fadd_rn(1.f, ex2_approx(z))), kFixOne);
+  return (uint32_t)__float_as_int(y) - kFixOneBits;
 }
 
 // Partial fixed-point F at boundary value e over components i0, i0 + di, ...
-// (di <= 4), four independent terms at a time; entries past the active ones
-// are zero.  (Handling the remainder exactly instead of padding it measured
-// slower: the larger code costs more than the skipped terms.)
+// (di <= 4), five independent terms at a time (the K = 10 mixture in two
+// rounds); entries past the active ones are zero, so the reads stay below
+// nact - 1 + 4 di + 1 <= 32 entries.  (Handling the remainder exactly
+// instead of padding it measured slower: the larger code costs more than
+// the skipped terms.)
 __device__ __forceinline__ uint32_t cdf_fix(const WarpScratch& ws, int nact, float e, int i0,
                                             int di) {
   uint32_t F = 0;
-  for (int i = i0; i < nact; i += 4 * di) {
+  for (int i = i0; i < nact; i += 5 * di) {
     const uint32_t t0 = cdf_term(e, ws.cp[i]);
     const uint32_t t1 = cdf_term(e, ws.cp[i + di]);
     const uint32_t t2 = cdf_term(e, ws.cp[i + 2 * di]);
     const uint32_t t3 = cdf_term(e, ws.cp[i + 3 * di]);
-    F += (t0 + t1) + (t2 + t3);
+    const uint32_t t4 = cdf_term(e, ws.cp[i + 4 * di]);
+    F += ((t0 + t1) + (t2 + t3)) + t4;
   }
   return F;
 }
@@ -488,13 +498,15 @@ __device__ __forceinline__ float channel_setup(const CompState& cs, int K, int c
   if (ch == 0) {
     if (gl < K) wS = __fmul_rn(fminf(exp_f(cs.logpi), 1.f), kFixOne);
   } else {
-    const float lw = gl < K ? cs.lw : -INFINITY;
+    const float lw = gl < K ? no_nan(cs.lw) : -INFINITY;
     const float mx = grp_max_r<GW>(lw);
     const uint32_t E = fix23(gl < K ? exp_f(__fsub_rn(lw, mx)) : 0.f);
     const uint32_t S = grp_isum<GW>(E);
     wS = fminf(__fmul_rn((float)E, __fmul_rn(kFixOne, rcp_approx((float)S))), kFixOne);
   }
-  const float m = gl < K ? comp_mean(cs, ch, r, g) : 0.f;
+  // the location within +-2^100 (a NaN network output becomes -2^100), so
+  // that every term is a number: past |m| = 2^100 the CDF is a step either way
+  const float m = gl < K ? fminf(fmaxf(comp_mean(cs, ch, r, g), -kMMax), kMMax) : 0.f;
   // the weights sum to one, so at least one component is active
   const bool on = gl < K && wS >= kWmin * kFixOne;
   const unsigned bits = grp_ballot<GW>(on);

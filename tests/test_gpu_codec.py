@@ -16,6 +16,7 @@ import torch
 import oracle as O
 from paper_2201_05213_gb300 import codec as CD
 from paper_2201_05213_gb300 import nlc as N
+from paper_2201_05213_gb300 import synth
 
 from gpu_util import DEV, ensure_built, images, make_codec, to_dev
 
@@ -49,6 +50,26 @@ def test_round_trip_all_schedules(prec, cfg, patch, layout):
     codec, _ = make_codec(cfg, prec, seed=5, scale=2.0)
     imgs = images(11, [(33, 41), (16, 16), (1, 7), (9, 1), (2, 2), (20, 3)])
     _round_trip(codec, imgs, patch, layout)
+
+
+@pytest.mark.parametrize("prec,cfg", [(N.NLC_FP32, (3, 32, 2, 10)), (N.NLC_BF16, (2, 32, 1, 10))])
+def test_round_trip_with_non_finite_network_outputs(prec, cfg):
+    # head biases set to NaN / +-inf make those outputs non-finite for every
+    # pixel (a logit, locations, a log-scale, a coupling coefficient): the
+    # tables stay valid, so the codec still round-trips
+    h, C, R, K = cfg
+    w = synth.xavier_weights(h, C, R, K, seed=7) * np.float32(2.0)
+    bH = w[len(w) - 10 * K:]
+    bH[3] = np.nan                # logit of component 3
+    bH[K + 2] = np.nan            # R location of component 2
+    bH[2 * K + 5] = np.inf        # G location of component 5
+    bH[4 * K + 1] = np.inf        # R log-scale of component 1
+    bH[5 * K + 4] = -np.inf       # G log-scale of component 4
+    bH[7 * K + 6] = np.nan        # a coupling coefficient of component 6
+    bH[9 * K + 8] = -np.inf
+    codec = CD.Codec(h, C, R, K, prec, w)
+    imgs = images(21, [(19, 23), (8, 8)])
+    _round_trip(codec, imgs, 0, 1, [N.NLC_SCHED_WAVEFRONT, N.NLC_SCHED_SEQUENTIAL])
 
 
 def test_edge_cases():

@@ -100,6 +100,24 @@ def test_tables_extreme_parameters():
     _check_tables(cum)
 
 
+def test_tables_non_finite_parameters():
+    # NaN and infinite network outputs (e.g. from corrupt weights) still give
+    # valid tables: the locations are bounded before the CDF, the weights and
+    # scales stay finite, so every term is a number and F stays monotone
+    cfg = (1, 16, 0, 10)
+    codec, _ = make_codec(cfg, N.NLC_FP32)
+    rng = np.random.default_rng(1)
+    n = 96
+    P = rng.normal(0, 3, (n, 100)).astype(np.float32)
+    bad = rng.random((n, 100)) < 0.2
+    P[bad] = rng.choice(np.array([np.nan, np.inf, -np.inf], dtype=np.float32), bad.sum())
+    P[:8] = np.nan  # whole rows
+    P[8:16, 10:40] = np.inf
+    pix = rng.integers(0, 256, (n, 3)).astype(np.uint8)
+    cum = codec.tables(torch.from_numpy(P).to(DEV), torch.from_numpy(pix).to(DEV)).cpu().numpy()
+    _check_tables(cum)
+
+
 def _rand_tables(rng, n):
     tabs = []
     for _ in range(n):
