@@ -611,21 +611,21 @@ __global__ void rans_dec_test_kernel(const uint8_t* __restrict__ in, long long s
   GroupRansDec dec;
   dec.bad = !fits;
   dec.x = kRansL;
-  dec.pos = 4;
-  dec.end = (unsigned long long)len;
+  unsigned long long pos = 4;
+  const unsigned long long end = (unsigned long long)len;
   if (!dec.bad)
     dec.x = ((uint32_t)base[0] << 24) | ((uint32_t)base[1] << 16) | ((uint32_t)base[2] << 8) |
             (uint32_t)base[3];
   for (long long k = sym_off[s]; k < sym_off[s + 1]; k++) {
     for (int b = lane; b < 256; b += 32) ws[warp].cum[cum_pos<32>(b)] = cum[k * 257 + b];
     __syncwarp();
-    dec.load_bytes(base);
+    dec.load_bytes(base, pos, end);
     const int v = dec.decode_table<32>(ws[warp], lane);
-    dec.pos += dec.used;
+    pos += dec.used;
     if (lane == 0) sym[k] = v;
     __syncwarp();
   }
-  if (lane == 0 && (dec.bad || dec.x != kRansL || dec.pos != dec.end)) set_status(status, ST_CORRUPT);
+  if (lane == 0 && (dec.bad || dec.x != kRansL || pos != end)) set_status(status, ST_CORRUPT);
 }
 
 cudaError_t launch_rans_decode(const uint8_t* in, long long stride, const int32_t* lens,

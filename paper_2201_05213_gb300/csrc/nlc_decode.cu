@@ -86,8 +86,7 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       dec.x = q.x;
       dec.lo = q.y;
       dec.hi = q.z;
-      dec.pos = pe.x;
-      dec.end = pe.y;
+      dec.set_avail(pe.x, pe.y);  // the positions are read again when the pixel is done
     }
     dec.w2 = dec.w3 = 0;
     dec.used = 0;
@@ -118,7 +117,8 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
     cp_async_wait_all();  // the window copies of the warp's lanes
     __syncwarp();
     if (gl == 0 && valid) {
-      dec.set_window(t.win + 4 * s);
+      const ulonglong2 pe = *reinterpret_cast<const ulonglong2*>(&t.rec[s].pos);
+      dec.set_window(t.win + 4 * s, pe.x);
       const Unit U = a.units[ps.unit];
       uint8_t* px = U.img + ((long long)(U.y0 + ps.i) * U.img_W + (U.x0 + ps.j)) * 3;
       px[0] = (uint8_t)v[0];
@@ -126,14 +126,14 @@ __device__ __noinline__ void code_tile(const DecodeArgs& a, const TileSmem& t, i
       px[2] = (uint8_t)v[2];
       if (SHEAR) ring_put(a, t.rofs[s], v);
       const int sid = ps.aux;
-      const unsigned long long np = dec.pos + (unsigned long long)dec.used;
+      const unsigned long long np = pe.x + (unsigned long long)dec.used;
       uint32_t n0, n1;
       dec.next_bytes(n0, n1);
       StreamRec* r = a.st + sid;
       *reinterpret_cast<uint4*>(r) = make_uint4(dec.x, n0, n1, 0u);
       r->pos = np;
       const bool last = a.layout == 1 ? (ps.j == U.Wu - 1) : (ps.i == U.Hu - 1 && ps.j == U.Wu - 1);
-      if (dec.bad || (last && (dec.x != kRansL || np != dec.end))) set_status(a.status, ST_CORRUPT);
+      if (dec.bad || (last && (dec.x != kRansL || np != pe.y))) set_status(a.status, ST_CORRUPT);
     }
   }
 }

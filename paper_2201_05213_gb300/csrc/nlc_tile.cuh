@@ -114,15 +114,15 @@ constexpr int kGroups = kThreads / kGW;
 // for the stream's next pixel takes its 8 bytes.
 struct GroupRansDec {
   uint32_t x;
-  unsigned long long pos, end;
   uint32_t lo, hi;  // bytes pos .. pos+7, little-endian packed
   uint32_t w2, w3;  // bytes pos+8 .. pos+15
   int used;
+  int avail;        // bytes of the stream left from pos, at most 8
   bool bad;
 
   // w2, w3 from the three aligned words at (pos + 8) & ~3 (a word is read
-  // only if it starts before `end`, so none outside the stream's container).
-  __device__ __forceinline__ void set_window(const uint32_t* v) {
+  // only if it starts before the stream's end, so none outside its container).
+  __device__ __forceinline__ void set_window(const uint32_t* v, unsigned long long pos) {
     const uint32_t sh = 8u * (uint32_t)((pos + 8ull) & 3ull);
     w2 = __funnelshift_r(v[0], v[1], sh);
     w3 = __funnelshift_r(v[1], v[2], sh);
@@ -139,8 +139,12 @@ struct GroupRansDec {
       n1 = __funnelshift_r(w2, w3, s);
     }
   }
+  __device__ __forceinline__ void set_avail(unsigned long long pos, unsigned long long end) {
+    avail = pos < end ? (int)min(end - pos, 8ull) : 0;
+  }
 
-  __device__ __forceinline__ void load_bytes(const uint8_t* base) {
+  __device__ __forceinline__ void load_bytes(const uint8_t* base, unsigned long long pos,
+                                             unsigned long long end) {
     lo = hi = 0;
 #pragma unroll
     for (int k = 0; k < 8; k++) {
@@ -149,6 +153,7 @@ struct GroupRansDec {
       if (k < 4) lo |= v << (8 * k);
       else hi |= v << (8 * (k - 4));
     }
+    set_avail(pos, end);
     used = 0;
   }
   // With slot = x mod 2^16 and the decoded symbol's cum_s <= slot < cum_{s+1}:
@@ -158,7 +163,7 @@ struct GroupRansDec {
     for (int it = 0; it < 3 && x < kRansL; it++) {
       const uint32_t bt = used < 4 ? (lo >> (8 * used)) & 0xFFu
                                    : used < 8 ? (hi >> (8 * (used - 4))) & 0xFFu : 0u;
-      if (used >= 8 || pos + (unsigned long long)used >= end) bad = true;
+      if (used >= avail) bad = true;
       x = (x << 8) | bt;
       used++;
     }
