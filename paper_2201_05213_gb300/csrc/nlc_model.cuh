@@ -442,13 +442,19 @@ __device__ __forceinline__ float comp_mean(const CompState& cs, int ch, int r, i
 // ---------------------------------------------------------------------
 
 // One component's term of F at boundary value e: the logistic is
-// 1/(1 + 2^z) with z = (m - e) log2(e)/s (no clamp: a z beyond the float
-// range of 2^z gives 2^z = +inf or +0, hence the term's limits 0 and w), and
-// the fused w sigmoid + 2^23, rounded once to nearest, is 2^23 + rint(w 2^23
-// sigmoid) (w 2^23 sigmoid lies in [0, 2^23], float spacing 1 in [2^23,
-// 2^24]), read back from its bits.
+// 1/(1 + 2^z) with z = (m - e) log2(e)/s (a z beyond the float range of 2^z
+// gives 2^z = +inf or +0, hence the term's limits 0 and w), and the fused
+// w sigmoid + 2^23, rounded once to nearest, is 2^23 + rint(w 2^23 sigmoid)
+// (w 2^23 sigmoid lies in [0, 2^23], float spacing 1 in [2^23, 2^24]), read
+// back from its bits.  kClamp clamps z to [-126, 126] first, which changes no
+// term: past 126 the term is 0 and below -126 it is rint(w) either way
+// (1 + 2^z rounds to 1).  The whole-warp search, one pixel per warp and bound
+// by latency, measured faster with the clamp; the 16-lane search, bound by
+// throughput, without it.
+template <bool kClamp = false>
 __device__ __forceinline__ uint32_t cdf_term(float e, const float4& p) {
-  const float z = __fmul_rn(__fsub_rn(p.x, e), p.y);
+  float z = __fmul_rn(__fsub_rn(p.x, e), p.y);
+  if (kClamp) z = fminf(fmaxf(z, -126.f), 126.f);
   const float y = __fmaf_rn(p.z, rcp_approx(__fadd_rn(1.f, ex2_approx(z))), kFixOne);
   return (uint32_t)__float_as_int(y) - kFixOneBits;
 }
@@ -459,15 +465,16 @@ __device__ __forceinline__ uint32_t cdf_term(float e, const float4& p) {
 // nact - 1 + 4 di + 1 <= 32 entries.  (Handling the remainder exactly
 // instead of padding it measured slower: the larger code costs more than
 // the skipped terms.)
+template <bool kClamp = false>
 __device__ __forceinline__ uint32_t cdf_fix(const WarpScratch& ws, int nact, float e, int i0,
                                             int di) {
   uint32_t F = 0;
   for (int i = i0; i < nact; i += 5 * di) {
-    const uint32_t t0 = cdf_term(e, ws.cp[i]);
-    const uint32_t t1 = cdf_term(e, ws.cp[i + di]);
-    const uint32_t t2 = cdf_term(e, ws.cp[i + 2 * di]);
-    const uint32_t t3 = cdf_term(e, ws.cp[i + 3 * di]);
-    const uint32_t t4 = cdf_term(e, ws.cp[i + 4 * di]);
+    const uint32_t t0 = cdf_term<kClamp>(e, ws.cp[i]);
+    const uint32_t t1 = cdf_term<kClamp>(e, ws.cp[i + di]);
+    const uint32_t t2 = cdf_term<kClamp>(e, ws.cp[i + 2 * di]);
+    const uint32_t t3 = cdf_term<kClamp>(e, ws.cp[i + 3 * di]);
+    const uint32_t t4 = cdf_term<kClamp>(e, ws.cp[i + 4 * di]);
     F += ((t0 + t1) + (t2 + t3)) + t4;
   }
   return F;
@@ -532,13 +539,13 @@ __device__ __forceinline__ int cdf_search(const WarpScratch& ws, int nact, uint3
   uint32_t u1 = 65536u;
   if (gl < GW - 1) {
     const int b = B * (gl + 1);
-    u1 = cum_fix(cdf_fix(ws, nact, edge_f(b), 0, 1), b);
+    u1 = cum_fix(cdf_fix<GW == 32>(ws, nact, edge_f(b), 0, 1), b);
   }
   const int c = __popc(grp_ballot<GW>(u1 <= slot));
   const int j = gl % B, part = gl / B;
   const int b2 = B * c + j + 1;
   uint32_t F2 = 0;
-  if (j < B - 1) F2 = cdf_fix(ws, nact, edge_f(b2), part, P);
+  if (j < B - 1) F2 = cdf_fix<GW == 32>(ws, nact, edge_f(b2), part, P);
 #pragma unroll
   for (int o = B; o < GW; o <<= 1) F2 += __shfl_xor_sync(full, F2, o, GW);
   const uint32_t top = __shfl_sync(full, u1, c, GW);  // cum_{B (c+1)}
