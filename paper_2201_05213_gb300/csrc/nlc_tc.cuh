@@ -714,7 +714,7 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
     __syncthreads();
   };
 
-  // layer 0: a = X W0^T + b0, H = ELU(a)
+  // layer 0: a = X W0^T + b0
   fence_async_smem();
   __syncthreads();
   tick(15);
@@ -722,29 +722,28 @@ __device__ __noinline__ bool tc_network(const Dims& d, TcSmem& t, int n_valid, l
   else tc_issue(t, (uint32_t)pl.p, (uint32_t)pl.w0, d.Fp, C);
   ok &= tc_wait(t);
   tick(14);
-  hidden(t.bias, 0);
-  for (int r = 0; r < d.R; r++) {
-    const float* b1 = t.bias + C + 2 * r * C;
-    // hidden = ELU(H W1^T + b1)
+  // The hidden layers' epilogues in order, each followed by the next layer's
+  // MMAs: layer 0 (H = ELU(a)), then per residual block r the inner layer
+  // (hidden = ELU(H W1^T + b1)) and the outer one (a += H W2^T + b2, H =
+  // ELU(a)); the last one is followed by the head, P = H WH^T + bH.  (One
+  // loop over the layers: written out per block, the same steps left the
+  // coding function, compiled in the same unit, with three times the spills.)
+  const int n_hidden = 1 + 2 * d.R;
+  for (int l = 0; l < n_hidden; l++) {
+    // layer l's biases: b0 at 0, then b1, b2 of block r at C + 2 r C, C + (2 r + 1) C
+    hidden(l == 0 ? t.bias : t.bias + C + (l - 1) * C, l == 0 ? 0 : ((l - 1) % 2 == 0 ? 2 : 1));
     tick(15);
-    tc_issue_ta(t, (uint32_t)pl.w1[r], C, C);
+    const int nl = l + 1;  // the layer issued next
+    if (nl == n_hidden)
+      tc_issue_ta(t, (uint32_t)pl.wh, C, d.NOp);
+    else
+      tc_issue_ta(t, (uint32_t)((nl - 1) % 2 == 0 ? pl.w1[(nl - 1) / 2] : pl.w2[(nl - 1) / 2]), C, C);
     ok &= tc_wait(t);
     tick(14);
-    hidden(b1, 2);
-    // a += H W2^T + b2, H = ELU(a)
-    tick(15);
-    tc_issue_ta(t, (uint32_t)pl.w2[r], C, C);
-    ok &= tc_wait(t);
-    tick(14);
-    hidden(b1 + C, 1);
   }
 
-  // head: P = H WH^T + bH, in batches of HB chunks
+  // head epilogue: P = acc + bH, in batches of HB chunks
   const float* bh = t.bias + C + 2 * d.R * C;
-  tick(15);
-  tc_issue_ta(t, (uint32_t)pl.wh, C, d.NOp);
-  ok &= tc_wait(t);
-  tick(14);
   if (live) {
     const int nh = d.NOp / 8;
     float* o = t.P + (size_t)row * d.ldP;
