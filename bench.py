@@ -57,12 +57,12 @@ def workload_name():
 
 
 # DRAM traffic of decode_kernel per decoded pixel from one ncu capture of the
-# small case at 16 CTAs (1x1024^2: 5.93 MB read + 0.51 MB written for
+# small case at 16 CTAs (1x1024^2: 5.86 MB read + 0.33 MB written for
 # 1,048,576 px), scaled to a launch by its pixels.  It holds only for the
 # kernel sources it was taken on: TRAFFIC_SRC_SHA is the sha256 of
 # DECODER_SOURCES, and any other sources report null.
-TRAFFIC_B_PER_PX = 6.15
-TRAFFIC_SRC_SHA = "d5d9f5131835c5e47d30e5a7af03b58408fb7b11d0c6642f67dbf1c83a47a592"
+TRAFFIC_B_PER_PX = 5.90
+TRAFFIC_SRC_SHA = "33b9820443fd66407b22614aad27fd7c6bd1f3f4797700392a48eacfbc364a78"
 
 
 # the sources decode_kernel is compiled from
