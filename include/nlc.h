@@ -123,10 +123,11 @@ size_t nlc_num_weights(const nlc_model_cfg* cfg);
 
 /* Creates a context on the current device with the given host weights
  * (n_weights must equal nlc_num_weights(cfg)).  Synchronous.  The first call
- * on a device also checks, over every pair of adjacent floats in the ranges
- * used, that the device's ex2.approx and rcp.approx are monotone (about a
- * millisecond); the frequency tables are computed one boundary at a time and
- * rely on it.  If the check fails: NLC_ERR_UNSUPPORTED. */
+ * on a device also checks, over every pair of adjacent floats (all floats for
+ * ex2.approx, [1, +inf] for rcp.approx), that the device's ex2.approx and
+ * rcp.approx are monotone (a few milliseconds); the frequency tables are
+ * computed one boundary at a time and rely on it.  If the check fails:
+ * NLC_ERR_UNSUPPORTED. */
 int nlc_create(const nlc_model_cfg* cfg, const float* h_weights, size_t n_weights, nlc_ctx** out);
 int nlc_destroy(nlc_ctx* ctx);
 
