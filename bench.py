@@ -66,8 +66,8 @@ TRAFFIC_SRC_SHA = "33b9820443fd66407b22614aad27fd7c6bd1f3f4797700392a48eacfbc364
 
 
 # the sources decode_kernel is compiled from
-DECODER_SOURCES = ["nlc_decode.cu", "nlc_tile.cuh", "nlc_tc.cuh", "nlc_model.cuh",
-                   "nlc_common.cuh", "nlc_kernels.cuh"]
+DECODER_SOURCES = ["nlc_decode.cu", "nlc_decode_kernel.cuh", "nlc_tile.cuh", "nlc_tc.cuh",
+                   "nlc_model.cuh", "nlc_common.cuh", "nlc_kernels.cuh"]
 
 
 def _csrc_sha():

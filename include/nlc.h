@@ -161,7 +161,9 @@ int nlc_set_wait_limits(nlc_ctx* ctx, uint32_t grid_polls, uint32_t mma_polls);
 /* Decoder phase profile (per-step latency against the dependency-bound step
  * count of Section 3).  enable != 0 makes the following nlc_decompress calls
  * and nlc_plan_run calls (a captured graph keeps the setting of its capture)
- * record, in thread 0 of every CTA, clock64 cycles spent per phase; a
+ * run an instrumented build of the decoder (same results, slower: its
+ * counters' state costs registers) that records, in thread 0 of every CTA,
+ * clock64 cycles spent per phase; a
  * non-NULL h_counters (16 uint64) receives the totals accumulated since the
  * last read, summed over CTAs, and clears them:
  *   [0] front bookkeeping, [1] tile slot assignment, [2] context gather and

@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnlc.so")
-SOURCES = ["nlc_codec.cu", "nlc_encode.cu", "nlc_decode.cu", "nlc_api.cu", "nlc_train.cu",
-           "nlc_train_tc.cu", "nlc_probe.cu"]
+SOURCES = ["nlc_codec.cu", "nlc_encode.cu", "nlc_decode.cu", "nlc_decode_prof.cu", "nlc_api.cu",
+           "nlc_train.cu", "nlc_train_tc.cu", "nlc_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr"]

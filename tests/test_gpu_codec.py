@@ -72,6 +72,38 @@ def test_round_trip_with_non_finite_network_outputs(prec, cfg):
     _round_trip(codec, imgs, 0, 1, [N.NLC_SCHED_WAVEFRONT, N.NLC_SCHED_SEQUENTIAL])
 
 
+def test_decode_profile_runs_the_instrumented_build():
+    # profiling switches decodes to the instrumented decoder (a plan made
+    # before it was switched on runs it too); its counters fill, and both
+    # builds decode the same pixels
+    codec, _ = make_codec((3, 64, 2, 10), N.NLC_BF16, seed=5)
+    imgs = images(31, [(64, 80), (40, 40)])
+    dimgs = [to_dev(i) for i in imgs]
+    data, offs = codec.compress(dimgs, 32, 1)
+    sizes = [i.shape[:2] for i in imgs]
+    plan = codec.plan(sizes, 32, 1)
+
+    def same(outs):
+        for a, b in zip(outs, imgs):
+            assert np.array_equal(a.cpu().numpy(), b)
+
+    plan.run(data, offs)
+    codec.check()
+    same(plan.outs)
+    N.nlc_decode_profile(codec.ctx, 1, read=False)
+    for o in plan.outs:
+        o.zero_()
+    plan.run(data, offs)
+    codec.check()
+    same(plan.outs)
+    cnt = N.nlc_decode_profile(codec.ctx, 0)  # read, clear, switch off
+    T = 32 + 31 * 4  # the largest unit's steps: 32 x 32 patches, h = 3
+    assert int(cnt[7]) == T and int(cnt[6]) >= 1
+    assert all(int(cnt[i]) > 0 for i in (0, 2, 3, 8, 9, 12, 13, 14, 15))
+    same(codec.decompress(data, offs, sizes, 32, 1))
+    assert int(N.nlc_decode_profile(codec.ctx, 0)[3]) == 0  # off: nothing recorded
+
+
 def test_edge_cases():
     codec, _ = make_codec((3, 32, 2, 10), N.NLC_FP32, seed=6)
     # empty batch
