@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kTT, 1)
   const uint32_t s0 = smem_u32(sm);
   uint32_t phase = 0;
   bool ok = true;
-  auto wait_mma = [&]() {  // the same verdict in every thread
+  auto wait_mma = [&]() {  // the same outcome in every thread
     if (threadIdx.x == 0) mma_commit(mbar);
     const bool done = mbar_wait(mbar, phase);
     phase ^= 1u;
