@@ -35,3 +35,15 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_recorded_traffic_matches_the_decoder_sources():
+    # the roofline's DRAM traffic per pixel comes from an ncu capture of the
+    # decoder; bench.py reports it only while the decoder's sources hash to
+    # the recorded value, so a change to them must come with a new capture
+    sys.path.insert(0, ROOT)
+    import bench
+    for name in bench.DECODER_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, "paper_2201_05213_gb300", "csrc", name)), name
+    assert bench._csrc_sha() == bench.TRAFFIC_SRC_SHA
+    assert 0 < bench.TRAFFIC_B_PER_PX < 64
