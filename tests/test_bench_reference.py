@@ -1,7 +1,9 @@
-"""The bench's reference arm (the FP64 oracle's sequential decoder on the host
-cores) prints one JSON line with the fields of the benchmark contract: the
-same metric, unit and workload as the GPU arm, a positive rate, the CPU
-baseline it measured and an end-to-end entry without device copies."""
+"""bench.py without a GPU: the reference arm (the FP64 oracle's sequential
+decoder on the host cores) prints one JSON line with the fields of the
+benchmark contract (the same metric, unit and workload as the GPU arm, a
+positive rate, the CPU baseline it measured and an end-to-end entry without
+device copies), and the decoder's recorded DRAM traffic belongs to the
+current decoder sources."""
 import json
 import os
 import subprocess
